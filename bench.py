@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free sum-factorized stiffness apply (GDoF/s).
+
+Workload (default): d = 3 perturbed unit cube, order p = 4, 64^3 elements
+(67^3 = 300,763 dofs, 256^3 Gauss points), a(x) = exp(0.5 sin 2 pi x cos 2 pi y),
+stiffness apply in FP32. One step = one apply v = K u (tile kernel + gather) with
+u, v and the factors resident in HBM. Factors (403 MB in FP32) exceed the L2
+(129 MB), so no flush is needed between steps.
+
+Also reported: the FP64 stiffness apply and both mass applies, the end-to-end
+rate through the host-buffer C-ABI call, the roofline of the tile kernel (its
+CUDA-event time on the launching stream over the timed region), the FP64 oracle
+timed on the host cores on a bounded sample of rows (and compared with the GPU
+result on those rows), and the SM clocks sampled during the timed region.
+
+With torchrun (N > 1) each rank runs its own replica of the workload on its own
+GPU (the apply of one patch does not shard: replicas only); value is the total
+over ranks divided by the slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D stiffness apply GDoF/s vs p and % HBM roofline; mixed vs FP64 at stated error"
+UNIT = "GDoF/s"
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="igasf", choices=["igasf", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--op", default="stiffness", choices=["stiffness", "mass"])
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--elements", type=int, default=64)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / mass side runs")
+    return ap.parse_args()
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def workload_name(p, K):
+    N = (K + p - 1) ** 3
+    return ("perturbed unit cube d=3, order p=%d, %d^3 elements (%d dofs, %d^3 Gauss points), "
+            "a=exp(0.5 sin 2pi x cos 2pi y), noise 0.2/%d, seed 0" % (p, K, N, p * K, K))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def algorithmic_bytes(op, prec, Qtot, N, d=3):
+    """Bytes the apply must move at minimum: the stored factors once, u once, v once."""
+    bf = 8 if prec == "fp64" else 4
+    nf = 1 if op == "mass" else d * (d + 1) // 2
+    return nf * bf * Qtot + 2 * bf * N
+
+
+def apply_flops(op, p, K, d=3):
+    """Floating-point operations of one sum-factorized apply at the global sizes
+    (tile halos excluded): forward sweeps, product, transposed sweeps."""
+    N1, Q1 = K + p - 1, K * p
+    if op == "mass":
+        fwd = 2 * p * (N1 * N1 * Q1 + N1 * Q1 * Q1 + Q1 ** 3)
+        return 2 * fwd + 1 * Q1 ** 3
+    fwd = 2 * p * (2 * N1 * N1 * Q1 + 3 * N1 * Q1 * Q1 + 3 * Q1 ** 3)
+    return 2 * fwd + 15 * Q1 ** 3
+
+
+def traffic_record(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the
+    current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_1809_05471_gb300", "csrc", "apply3d.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = rec.get(kernel_key)
+    if not ent or ent.get("apply3d_cuh_sha256_16") != h:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+def _smi_id():
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return "%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        return vis if vis.isdigit() else "0"
+
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--id=" + _smi_id(), "--query-gpu=" + QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(REASONS, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline); the only oracle use in this file
+# ---------------------------------------------------------------------------
+def cpu_baseline(patch, op_code, u, seconds, v_gpu=None, seed=0):
+    import numpy as np
+    import oracle as O
+
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(seed)
+    t_rows = 0.0
+    done = 0
+    batch = 4 * cores
+    rows_all, v_all, ra_all = [], [], []
+    while t_rows < seconds:
+        rows = np.sort(rng.choice(patch.num_dofs, size=batch, replace=False))
+        t0 = time.perf_counter()
+        v, ra = O.apply_rows(patch, op_code, u, rows, threads=cores)
+        t_rows += time.perf_counter() - t0
+        done += len(rows)
+        rows_all.append(rows)
+        v_all.append(v)
+        ra_all.append(ra)
+        if t_rows < seconds / 4:
+            batch *= 2
+    rows = np.concatenate(rows_all)
+    vref = np.concatenate(v_all)
+    a_inf = float(np.concatenate(ra_all).max())
+    res = {"value": done / t_rows / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%d random rows of v = A u, each assembled from the definition "
+                     "(row-wise oracle, OpenMP over rows), %.1f s" % (done, t_rows)}
+    errs = {}
+    if v_gpu:
+        uinf = float(np.max(np.abs(u)))
+        for key, vg in v_gpu.items():
+            errs[key] = float(np.max(np.abs(vg[rows] - vref))) / (a_inf * uinf)
+    return res, errs
+
+
+# ---------------------------------------------------------------------------
+def run_igasf(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1809_05471_gb300 import igasf as G
+    from paper_1809_05471_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    p, K = args.p, args.elements
+    patch, u = I.config_cube(p=p, K=K)
+    t0 = time.perf_counter()
+    plan = G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    N, Qtot = plan.num_dofs, plan.num_quad_points
+    dt = {"fp32": torch.float32, "fp64": torch.float64}
+    pc = {"fp32": G.FP32, "fp64": G.FP64}
+    oc = {"stiffness": G.STIFFNESS, "mass": G.MASS}
+    stream = torch.cuda.current_stream()
+
+    def timed(op, prec, steps, warmup, sample_clocks=False):
+        ud = torch.as_tensor(u, device="cuda").to(dt[prec])
+        vd = torch.empty_like(ud)
+        for _ in range(warmup):
+            plan.apply(oc[op], ud, vd, prec=pc[prec], stream=stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = ClockSampler() if sample_clocks and rank == 0 else None
+        if clocks is not None:
+            time.sleep(0.3)   # let the sampler start before the timed region
+        plan.profile_begin(steps)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(steps):
+            plan.apply(oc[op], ud, vd, prec=pc[prec], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        k_ms, g_ms, n_timed = plan.profile_end()
+        ck = clocks.stop() if clocks is not None else None
+        if world > 1:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, k_ms / max(n_timed, 1), g_ms / max(n_timed, 1), vd, ck
+
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+
+    def roofline(op, prec, kernel_ms):
+        ab = algorithmic_bytes(op, prec, Qtot, N)
+        ach = ab / (kernel_ms * 1e-3) / 1e9
+        r = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+             "frac": round(ach / hbm, 4), "traffic": traffic_record("%s_%s_p%d" % (op, prec, p)),
+             "algorithmic_bytes_per_launch": ab, "kernel_ms": round(kernel_ms, 5),
+             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src}
+        if prec == "fp64":
+            fl = apply_flops(op, p, K)
+            r["fp64_tflops"] = round(fl / (kernel_ms * 1e-3) / 1e12, 3)
+        return r
+
+    # headline
+    ms, k_ms, g_ms, vd, clocks = timed(args.op, args.prec, args.steps, args.warmup, True)
+    per_step = ms / args.steps
+    value = world * N / (per_step * 1e-3) / 1e9
+    v_main = vd.double().cpu().numpy()
+
+    # end to end through the host-buffer call (pinned host memory)
+    uh = torch.as_tensor(u).to(dt[args.prec]).pin_memory()
+    vh = torch.empty_like(uh).pin_memory()
+    for _ in range(max(3, min(args.warmup, 20))):
+        plan.apply_host(oc[args.op], uh, vh, prec=pc[args.prec], stream=stream)
+    e2e_steps = max(10, min(args.steps, 2000))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.apply_host(oc[args.op], uh, vh, prec=pc[args.prec], stream=stream)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    bio = 4 if args.prec == "fp32" else 8
+    e2e = {"value": round(world * N * e2e_steps / e2e_s / 1e9, 4), "unit": UNIT,
+           "h2d_bytes_per_step": N * bio, "d2h_bytes_per_step": N * bio,
+           "ms_per_step": round(e2e_s / e2e_steps * 1e3, 4),
+           "api": "igasf_apply_host (pinned host u, v)"}
+
+    extra = []
+    v_gpu = {"%s_%s" % (args.op, args.prec): v_main}
+    if not args.no_extra:
+        for op, prec in (("stiffness", "fp64"), ("mass", "fp32"), ("mass", "fp64"),
+                         ("stiffness", "fp32")):
+            if (op, prec) == (args.op, args.prec):
+                continue
+            steps = 300 if prec == "fp64" else 1000
+            ms2, k2, g2, vd2, _ = timed(op, prec, steps, 10)
+            if op == args.op:
+                v_gpu["%s_%s" % (op, prec)] = vd2.double().cpu().numpy()
+            extra.append({"op": op, "prec": prec, "value": round(world * N / (ms2 / steps * 1e-3) / 1e9, 4),
+                          "ms_per_step": round(ms2 / steps, 5), "roofline": roofline(op, prec, k2),
+                          "gather_ms": round(g2, 5)})
+
+    result = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": workload_name(p, K), "op": args.op, "precision": args.prec,
+                   "d": 3, "order": p, "elements_per_dir": K, "dofs": N, "quad_points": Qtot,
+                   "tile": plan.describe(pc[args.prec])["tile"],
+                   "l2": "no flush: factors (%.0f MB) larger than L2 (129 MB)"
+                         % (algorithmic_bytes(args.op, args.prec, Qtot, 0) / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline(args.op, args.prec, k_ms),
+        "gather_ms": round(g_ms, 5),
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps * world,
+        "setup_s": round(setup_s, 3),
+        "clocks": clocks,
+        "also": extra,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, errs = cpu_baseline(patch, oc[args.op], u, args.cpu_seconds, v_gpu)
+        result["cpu_baseline"] = cb
+        result["error_vs_oracle"] = {"rows": "the cpu_baseline sample", "scaled_max_norm": errs,
+                                     "tolerance": TOL}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores, on the same workload and metric:
+    each step computes a bounded sample of rows of v = A u."""
+    import numpy as np
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1809_05471_gb300 import inputs as I
+
+    p, K = args.p, args.elements
+    patch, u = I.config_cube(p=p, K=K)
+    op = O.STIFFNESS if args.op == "stiffness" else O.MASS
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(0)
+    # size each step so that warmup + steps take about 120 s
+    t0 = time.perf_counter()
+    O.apply_rows(patch, op, u, rng.choice(patch.num_dofs, cores, replace=False), threads=cores)
+    per_row = (time.perf_counter() - t0) / cores
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    rows_per_step = max(1, int(budget / per_row))
+    for _ in range(args.warmup):
+        O.apply_rows(patch, op, u, rng.choice(patch.num_dofs, rows_per_step, replace=False),
+                     threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.apply_rows(patch, op, u, rng.choice(patch.num_dofs, rows_per_step, replace=False),
+                     threads=cores)
+    dt_s = time.perf_counter() - t0
+    value = rows_per_step * args.steps / dt_s / 1e9
+    sample = ("%d random rows of v = A u per step (row-wise FP64 oracle, OpenMP over rows)"
+              % rows_per_step)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(p, K), "op": args.op, "precision": args.prec},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_igasf(args)
+
+
+if __name__ == "__main__":
+    main()

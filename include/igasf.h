@@ -1,0 +1,207 @@
+/*
+ * igasf: matrix-free, sum-factorized isogeometric mass and stiffness operators
+ * on one GB300 (sm_103a).
+ *
+ * The operator is the quadrature approximation of the bilinear form
+ * (Sec. 2, eq. quadrature:1):
+ *
+ *     A_mn = sum_{x in X} w(x) F(x) d^theta phi_n(x) d^eta phi_m(x)
+ *
+ * for tensor-product B-splines phi_n of order p (degree + 1) on open knot
+ * vectors, Gauss quadrature with p points per element per direction
+ * (Example gauss), and the pull-back coefficient of Example 1 (eq. cdr:1)
+ * for a geometry map G = sum_n c_n phi_n (Sec. 6.2):
+ *
+ *     mass       (theta = eta = 0):  F = |det J|
+ *     stiffness  (|theta|=|eta|=1):  F = a(G(x)) |det J| J^-1 J^-T,
+ *                                    J_ij = dG_i / dxi_j.
+ *
+ * v = A u is applied without forming A, by the matrix-free sum factorization
+ * of Alg. 2 and Alg. 3 (d directional sweeps dofs -> quadrature points, the
+ * pointwise product with the precomputed factors w F, and d transposed sweeps
+ * back), localized to macro-element tiles as in Sec. 4 (eq. loc-basis-change:
+ * A = sum_D S_D^T A_D S_D).
+ *
+ * Conventions for every entry point:
+ *   - Dofs are lexicographic with the first index fastest (Sec. 3.1, the
+ *     ordering pi): n = n_1 + N_1 (n_2 + N_2 n_3). Quadrature points likewise.
+ *   - Return value: IGASF_OK (0) or a negative igasf_status. On error
+ *     igasf_last_error_message() describes it (per host thread).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Device pointers are plain CUDA device addresses on the device
+ *     that was current when igasf_setup ran; that device must be current for
+ *     every later call on the handle.
+ *   - A handle may be used from one host thread / one stream at a time.
+ */
+#ifndef IGASF_H
+#define IGASF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IGASF_VERSION 1
+#define IGASF_MAX_DIM 3
+/* Orders the CUDA kernels are built for: 2 <= p <= IGASF_MAX_ORDER. */
+#define IGASF_MAX_ORDER 9
+
+typedef enum {
+  IGASF_OK = 0,
+  IGASF_ERR_INVALID_ARG = -1, /* null/misaligned pointer, bad enum or size */
+  IGASF_ERR_KNOTS = -2,       /* knot vector not open, decreasing, or too short */
+  IGASF_ERR_GEOMETRY = -3,    /* det J <= 0 at some quadrature point */
+  IGASF_ERR_UNSUPPORTED = -4, /* valid input the GPU path does not handle */
+  IGASF_ERR_CUDA = -5,        /* a CUDA runtime call or kernel launch failed */
+  IGASF_ERR_OOM = -6,         /* device or host allocation failed */
+  IGASF_ERR_TIMEOUT = -7      /* a bounded device wait gave up */
+} igasf_status;
+
+typedef enum { IGASF_MASS = 0, IGASF_STIFFNESS = 1 } igasf_op;
+
+/* Arithmetic of an apply. FP64: FP64 factors, tables and vectors.
+ * FP32: FP32 factors, tables, vectors and arithmetic (factors are computed in
+ * FP64 at setup and rounded once). */
+typedef enum { IGASF_FP64 = 0, IGASF_FP32 = 1 } igasf_prec;
+#define IGASF_PREC_BIT(prec) (1u << (unsigned)(prec))
+
+/* Coefficient a of the stiffness operator (Example 1 with A = a I, evaluated
+ * at the physical point G(x)); the mass operator ignores it. */
+typedef enum {
+  IGASF_COEF_CONSTANT = 0,    /* a = constant */
+  IGASF_COEF_EXP_SIN_COS = 1, /* a = exp(alpha sin(2 pi x_1) cos(2 pi x_2)), cos term = 1 for d = 1 */
+  IGASF_COEF_VALUES = 2       /* a given per quadrature point (host array, lexicographic) */
+} igasf_coef_kind;
+
+typedef struct {
+  int kind;              /* igasf_coef_kind */
+  double constant;       /* IGASF_COEF_CONSTANT */
+  double alpha;          /* IGASF_COEF_EXP_SIN_COS */
+  const double *values;  /* IGASF_COEF_VALUES: host, igasf_num_quad_points() values; copied */
+} igasf_coef;
+
+/* Zero-initialised = defaults. */
+typedef struct {
+  unsigned precisions;   /* bitmask of IGASF_PREC_BIT(prec) whose factors setup stores;
+                            0 = only default_prec */
+  int default_prec;      /* precision used by igasf_apply (default IGASF_FP64) */
+  int tile[3];           /* elements per tile per direction, 0 = the library's choice;
+                            honoured only where a kernel is built for that shape */
+  int reserved[8];       /* must be zero */
+} igasf_options;
+
+typedef struct igasf_plan *igasf_handle;
+
+/* Static description of a plan for one precision. */
+typedef struct {
+  int d, order;
+  int tile[3];              /* elements per tile per direction (1 in unused directions) */
+  int tiles[3];             /* tiles per direction */
+  int threads_per_block;
+  int64_t num_dofs;
+  int64_t num_quad_points;
+  int64_t factor_bytes[2];  /* stored factor bytes for [IGASF_MASS], [IGASF_STIFFNESS],
+                               including the zero padding of ragged tiles */
+  int64_t workspace_bytes;  /* per-tile partial results of v */
+  size_t smem_bytes[2];     /* dynamic shared memory per block, [op] */
+} igasf_plan_desc;
+
+/*
+ * Build a plan: univariate tables (Sec. 6.1), the geometry factors w F at all
+ * quadrature points (Sec. 6.2; computed in FP64 on the device by sum-factorized
+ * evaluation of G and its derivatives, Alg. 3), and the workspace. Blocks until
+ * the factors are computed and checked.
+ *
+ *   d            dimension, 2 or 3.
+ *   orders       host, d ints: order p per direction (all equal, 2..IGASF_MAX_ORDER).
+ *   knot_lengths host, d ints: entries of each knot vector.
+ *   knots        host, d pointers to non-decreasing open knot vectors (first and
+ *                last knot repeated p times). The GPU path needs simple interior
+ *                knots (multiplicity 1); repeated ones give IGASF_ERR_UNSUPPORTED.
+ *   ctrl         host, N*d doubles: control point n at ctrl[n*d .. n*d+d-1].
+ *   coef         host, may be NULL (= constant 1).
+ *   opt          host, may be NULL (= defaults).
+ *   out          receives the handle; untouched on error.
+ * All host inputs are copied; the caller may free them on return.
+ * Errors: INVALID_ARG, KNOTS, GEOMETRY (det J <= 0 somewhere), UNSUPPORTED,
+ * CUDA, OOM. Nothing is leaked on error.
+ */
+int igasf_setup(int d, const int *orders, const int *knot_lengths, const double *const *knots,
+                const double *ctrl, const igasf_coef *coef, const igasf_options *opt,
+                igasf_handle *out);
+
+/*
+ * v = A u on `stream` in the handle's default precision (Alg. 2 after Alg. 3,
+ * localized per Sec. 4). u and v: device arrays of num_dofs values of the
+ * precision's type (double for FP64, float for FP32), aligned to that type,
+ * not overlapping. v is overwritten. Asynchronous: returns after enqueueing; it
+ * allocates nothing and does not synchronise. Errors: INVALID_ARG (null or
+ * misaligned pointer, bad op), UNSUPPORTED (precision not stored at setup),
+ * CUDA (launch failure).
+ */
+int igasf_apply(igasf_handle h, int op, const void *u, void *v, void *stream);
+
+/* As igasf_apply, with the precision given explicitly. */
+int igasf_apply_prec(igasf_handle h, int op, int prec, const void *u, void *v, void *stream);
+
+/*
+ * As igasf_apply_prec with HOST arrays u and v (pinned memory gives the
+ * fastest copies): copies u to the plan's device staging buffer, applies, copies
+ * the result back and waits for `stream`. The staging buffers are allocated at
+ * setup. Synchronous.
+ */
+int igasf_apply_host(igasf_handle h, int op, int prec, const void *u_host, void *v_host,
+                     void *stream);
+
+/* Synchronise the device and free everything the handle owns. NULL is a no-op. */
+int igasf_destroy(igasf_handle h);
+
+int64_t igasf_num_dofs(igasf_handle h);          /* -1 on a NULL handle */
+int64_t igasf_num_quad_points(igasf_handle h);   /* -1 on a NULL handle */
+
+/* Plan description for one stored precision. */
+int igasf_describe(igasf_handle h, int prec, igasf_plan_desc *out);
+
+/*
+ * Univariate tables of direction `dir` (0-based) as computed on the device, in
+ * FP64 (Sec. 6.1): nodes[Q], weights[Q], B[Q*p], dB[Q*p] with Q = K*p, where
+ * B[q*p + j] is the value of the j-th function active on the element of
+ * quadrature point q (function index = element index + j for simple knots) and
+ * dB its derivative. Host outputs; any may be NULL. Synchronous.
+ */
+int igasf_get_tables(igasf_handle h, int dir, double *nodes, double *weights, double *B,
+                     double *dB);
+
+/*
+ * The stored factors w F of `op` at precision `prec`, converted to FP64, in
+ * lexicographic quadrature order: mass out[q]; stiffness out[q*nf + f] with
+ * nf = d(d+1)/2 upper-triangle entries in row order (11,12,13,22,23,33 or
+ * 11,12,22). Host output of num_quad_points*nf doubles. Synchronous.
+ */
+int igasf_get_factors(igasf_handle h, int op, int prec, double *out);
+
+/*
+ * Per-kernel timing with CUDA events, for benchmarks. igasf_profile_begin
+ * creates events for up to `max_applies` later applies on this handle; each of
+ * those applies then records an event before its tile kernel, between the tile
+ * kernel and the gather, and after the gather, on the apply's own stream.
+ * igasf_profile_end waits for the events, returns the summed durations in
+ * milliseconds (ms[0] tile kernel, ms[1] gather) and the number of applies
+ * timed, and destroys the events. Applies beyond max_applies are not timed.
+ * Errors: INVALID_ARG, CUDA, OOM.
+ */
+int igasf_profile_begin(igasf_handle h, int max_applies);
+int igasf_profile_end(igasf_handle h, double *ms, int *applies);
+
+/* Message for the last error on this host thread ("" if none). */
+const char *igasf_last_error_message(void);
+
+int igasf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IGASF_H */

@@ -1,0 +1,546 @@
+// C ABI of libigasf: argument validation, plan lifetime, dispatch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "igasf.h"
+#include "igasf_internal.h"
+
+using namespace igasf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(IGASF_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(IGASF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct Variant {
+  bool present = false;
+  ApplyKernel k{};
+  FactorLayout L{};
+  void *tabB[kMaxDim] = {nullptr, nullptr, nullptr};
+  void *tabD[kMaxDim] = {nullptr, nullptr, nullptr};
+  int T[kMaxDim] = {1, 1, 1};
+  int Qpad[kMaxDim] = {0, 0, 0};
+  int ntiles = 0;
+  size_t bytesM = 0, bytesK = 0;
+  void *vpart = nullptr;
+  size_t vpart_bytes = 0;
+  void *u_stage = nullptr, *v_stage = nullptr;
+};
+
+}  // namespace
+
+struct igasf_plan {
+  int d = 0, p = 0, device = 0;
+  int N[kMaxDim] = {1, 1, 1}, K[kMaxDim] = {1, 1, 1}, Q[kMaxDim] = {1, 1, 1};
+  int64_t Ntot = 0, Qtot = 0;
+  double *knots[kMaxDim] = {nullptr, nullptr, nullptr};
+  int *span[kMaxDim] = {nullptr, nullptr, nullptr};
+  double *nodes[kMaxDim] = {nullptr, nullptr, nullptr};
+  double *weights[kMaxDim] = {nullptr, nullptr, nullptr};
+  double *tabB[kMaxDim] = {nullptr, nullptr, nullptr};  // FP64 [j][Q]
+  double *tabD[kMaxDim] = {nullptr, nullptr, nullptr};
+  int default_prec = IGASF_FP64;
+  Variant var[kNumPrec];
+  std::vector<cudaEvent_t> prof_events;  // 3 per timed apply
+  int prof_next = 0;                     // applies recorded so far
+};
+
+namespace {
+
+void destroy_events(igasf_plan *h) {
+  for (cudaEvent_t e : h->prof_events) cudaEventDestroy(e);
+  h->prof_events.clear();
+  h->prof_next = 0;
+}
+
+void free_plan(igasf_plan *h) {
+  if (!h) return;
+  destroy_events(h);
+  for (int a = 0; a < kMaxDim; ++a) {
+    cudaFree(h->knots[a]);
+    cudaFree(h->span[a]);
+    cudaFree(h->nodes[a]);
+    cudaFree(h->weights[a]);
+    cudaFree(h->tabB[a]);
+    cudaFree(h->tabD[a]);
+  }
+  for (auto &v : h->var) {
+    cudaFree(v.L.DM);
+    cudaFree(v.L.DK);
+    for (int a = 0; a < kMaxDim; ++a) {
+      cudaFree(v.tabB[a]);
+      cudaFree(v.tabD[a]);
+    }
+    cudaFree(v.vpart);
+    cudaFree(v.u_stage);
+    cudaFree(v.v_stage);
+  }
+  delete h;
+}
+
+size_t prec_size(int prec) { return prec == IGASF_FP64 ? sizeof(double) : sizeof(float); }
+
+// Validate one open knot vector; count elements. Returns IGASF_OK or an error.
+int check_knots(int dir, int p, int nk, const double *t, int *K_out) {
+  if (!t) return fail(IGASF_ERR_INVALID_ARG, "knots[%d] is NULL", dir);
+  if (nk < 2 * p) return fail(IGASF_ERR_KNOTS, "knot vector %d has %d entries, needs >= %d", dir, nk, 2 * p);
+  for (int i = 0; i < nk; ++i)
+    if (!(t[i] == t[i]) || t[i] - t[i] != 0.0)
+      return fail(IGASF_ERR_KNOTS, "knot vector %d has a non-finite entry", dir);
+  for (int i = 0; i + 1 < nk; ++i)
+    if (t[i + 1] < t[i]) return fail(IGASF_ERR_KNOTS, "knot vector %d decreases at %d", dir, i);
+  for (int i = 1; i < p; ++i)
+    if (t[i] != t[0] || t[nk - 1 - i] != t[nk - 1])
+      return fail(IGASF_ERR_KNOTS, "knot vector %d is not open (ends need multiplicity %d)", dir, p);
+  if (t[p] == t[0]) return fail(IGASF_ERR_KNOTS, "knot vector %d: first knot repeated more than p times", dir);
+  if (t[nk - 1 - p] == t[nk - 1]) return fail(IGASF_ERR_KNOTS, "knot vector %d: last knot repeated more than p times", dir);
+  if (!(t[nk - 1] > t[0])) return fail(IGASF_ERR_KNOTS, "knot vector %d spans an empty interval", dir);
+  int K = 0;
+  for (int i = p; i < nk - p;) {
+    int m = 1;
+    while (i + m < nk - p && t[i + m] == t[i]) ++m;
+    if (m >= p) return fail(IGASF_ERR_KNOTS, "knot vector %d: interior multiplicity %d >= order %d", dir, m, p);
+    if (m > 1)
+      return fail(IGASF_ERR_UNSUPPORTED,
+                  "knot vector %d: repeated interior knot (multiplicity %d); the GPU path needs simple knots", dir, m);
+    i += m;
+  }
+  K = nk - 2 * p + 1;
+  *K_out = K;
+  return IGASF_OK;
+}
+
+int alloc(void **p, size_t bytes, const char *what) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, what);
+  }
+  return IGASF_OK;
+}
+
+#define TRY(x)                  \
+  do {                          \
+    int rc_ = (x);              \
+    if (rc_ != IGASF_OK) {      \
+      free_plan(h);             \
+      return rc_;               \
+    }                           \
+  } while (0)
+
+#define TRY_CUDA(x, what)                   \
+  do {                                      \
+    cudaError_t e_ = (x);                   \
+    if (e_ != cudaSuccess) {                \
+      int rc_ = cuda_fail(e_, what);        \
+      free_plan(h);                         \
+      return rc_;                           \
+    }                                       \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int igasf_version(void) { return IGASF_VERSION; }
+
+const char *igasf_last_error_message(void) { return g_last_error.c_str(); }
+
+int igasf_setup(int d, const int *orders, const int *knot_lengths, const double *const *knots,
+                const double *ctrl, const igasf_coef *coef, const igasf_options *opt,
+                igasf_handle *out) {
+  g_last_error.clear();
+  if (!out) return fail(IGASF_ERR_INVALID_ARG, "out is NULL");
+  if (d != 2 && d != 3) return fail(IGASF_ERR_UNSUPPORTED, "d = %d; supported: 2, 3", d);
+  if (!orders || !knot_lengths || !knots || !ctrl)
+    return fail(IGASF_ERR_INVALID_ARG, "orders, knot_lengths, knots and ctrl must be non-NULL");
+  const int p = orders[0];
+  for (int a = 0; a < d; ++a) {
+    if (orders[a] < 1) return fail(IGASF_ERR_INVALID_ARG, "order %d in direction %d", orders[a], a);
+    if (orders[a] != p) return fail(IGASF_ERR_UNSUPPORTED, "orders differ between directions");
+  }
+  if (p < 2 || p > IGASF_MAX_ORDER)
+    return fail(IGASF_ERR_UNSUPPORTED, "order p = %d; kernels are built for 2..%d", p, IGASF_MAX_ORDER);
+  igasf_options o;
+  memset(&o, 0, sizeof(o));
+  if (opt) o = *opt;
+  for (int r : o.reserved)
+    if (r != 0) return fail(IGASF_ERR_INVALID_ARG, "options.reserved must be zero");
+  if (o.default_prec != IGASF_FP64 && o.default_prec != IGASF_FP32)
+    return fail(IGASF_ERR_INVALID_ARG, "options.default_prec = %d", o.default_prec);
+  unsigned precs = o.precisions ? o.precisions : IGASF_PREC_BIT(o.default_prec);
+  if (precs & ~(IGASF_PREC_BIT(IGASF_FP64) | IGASF_PREC_BIT(IGASF_FP32)))
+    return fail(IGASF_ERR_INVALID_ARG, "options.precisions has unknown bits 0x%x", precs);
+  if (!(precs & IGASF_PREC_BIT(o.default_prec)))
+    return fail(IGASF_ERR_INVALID_ARG, "options.precisions must include default_prec");
+  igasf_coef c;
+  c.kind = IGASF_COEF_CONSTANT;
+  c.constant = 1.0;
+  c.alpha = 0.0;
+  c.values = nullptr;
+  if (coef) c = *coef;
+  if (c.kind < IGASF_COEF_CONSTANT || c.kind > IGASF_COEF_VALUES)
+    return fail(IGASF_ERR_INVALID_ARG, "coef.kind = %d", c.kind);
+  if (c.kind == IGASF_COEF_VALUES && !c.values)
+    return fail(IGASF_ERR_INVALID_ARG, "coef.values is NULL");
+  int K[kMaxDim] = {1, 1, 1};
+  for (int a = 0; a < d; ++a) {
+    int rc = check_knots(a, p, knot_lengths[a], knots[a], &K[a]);
+    if (rc != IGASF_OK) return rc;
+  }
+  // which kernels
+  ApplyKernel kern[kNumPrec];
+  for (int prec = 0; prec < kNumPrec; ++prec) {
+    if (!(precs & IGASF_PREC_BIT(prec))) continue;
+    if (!find_apply_kernel(d, p, prec, &kern[prec]))
+      return fail(IGASF_ERR_UNSUPPORTED, "no kernel for d=%d p=%d prec=%d", d, p, prec);
+    for (int a = 0; a < d; ++a)
+      if (o.tile[a] != 0 && o.tile[a] != kern[prec].S[a])
+        return fail(IGASF_ERR_UNSUPPORTED, "tile[%d] = %d is not a built shape (built: %d)", a, o.tile[a],
+                    kern[prec].S[a]);
+  }
+  // host-side validation done: now the device
+  igasf_plan *h = new (std::nothrow) igasf_plan();
+  if (!h) return fail(IGASF_ERR_OOM, "host allocation");
+  h->d = d;
+  h->p = p;
+  h->default_prec = o.default_prec;
+  TRY_CUDA(cudaGetDevice(&h->device), "cudaGetDevice");
+  h->Ntot = 1;
+  h->Qtot = 1;
+  for (int a = 0; a < d; ++a) {
+    h->K[a] = K[a];
+    h->N[a] = knot_lengths[a] - p;
+    h->Q[a] = K[a] * p;
+    h->Ntot *= h->N[a];
+    h->Qtot *= h->Q[a];
+  }
+  cudaStream_t s = nullptr;
+  // knots, spans, tables
+  for (int a = 0; a < d; ++a) {
+    const int nk = knot_lengths[a], Qa = h->Q[a];
+    std::vector<int> span(K[a]);
+    for (int e = 0; e < K[a]; ++e) span[e] = p - 1 + e;
+    TRY(alloc((void **)&h->knots[a], sizeof(double) * nk, "knots"));
+    TRY(alloc((void **)&h->span[a], sizeof(int) * K[a], "spans"));
+    TRY(alloc((void **)&h->nodes[a], sizeof(double) * Qa, "nodes"));
+    TRY(alloc((void **)&h->weights[a], sizeof(double) * Qa, "weights"));
+    TRY(alloc((void **)&h->tabB[a], sizeof(double) * Qa * p, "tables"));
+    TRY(alloc((void **)&h->tabD[a], sizeof(double) * Qa * p, "tables"));
+    TRY_CUDA(cudaMemcpy(h->knots[a], knots[a], sizeof(double) * nk, cudaMemcpyHostToDevice), "copy knots");
+    TRY_CUDA(cudaMemcpy(h->span[a], span.data(), sizeof(int) * K[a], cudaMemcpyHostToDevice), "copy spans");
+    TRY_CUDA(launch_tables(p, K[a], h->knots[a], h->span[a], h->nodes[a], h->weights[a], h->tabB[a],
+                           h->tabD[a], s),
+             "tables kernel");
+  }
+  // per-precision layouts, tables, workspace
+  GeometryParams g;
+  memset(&g, 0, sizeof(g));
+  for (int prec = 0; prec < kNumPrec; ++prec) {
+    if (!(precs & IGASF_PREC_BIT(prec))) continue;
+    Variant &v = h->var[prec];
+    v.present = true;
+    v.k = kern[prec];
+    const size_t es = prec_size(prec);
+    v.ntiles = 1;
+    int64_t vol = 1;
+    for (int a = 0; a < kMaxDim; ++a) v.T[a] = 1;
+    for (int a = 0; a < d; ++a) {
+      v.T[a] = (K[a] + v.k.S[a] - 1) / v.k.S[a];
+      v.Qpad[a] = v.T[a] * v.k.S[a] * p;
+      v.ntiles *= v.T[a];
+      vol *= v.k.S[a] + p - 1;
+    }
+    v.L.d = d;
+    v.L.p = p;
+    for (int a = 0; a < kMaxDim; ++a) {
+      v.L.S[a] = a < d ? v.k.S[a] : 1;
+      v.L.T[a] = v.T[a];
+    }
+    v.L.plane = v.k.plane;
+    v.L.is_fp32 = prec == IGASF_FP32;
+    const int64_t Qlast = (int64_t)v.k.S[d - 1] * p;
+    const int64_t rows = (int64_t)v.ntiles * Qlast;
+    v.bytesM = (size_t)rows * 1 * v.L.plane * es;
+    v.bytesK = (size_t)rows * num_fields(d, IGASF_STIFFNESS) * v.L.plane * es;
+    TRY(alloc(&v.L.DM, v.bytesM, "mass factors"));
+    TRY(alloc(&v.L.DK, v.bytesK, "stiffness factors"));
+    TRY_CUDA(cudaMemsetAsync(v.L.DM, 0, v.bytesM, s), "memset");
+    TRY_CUDA(cudaMemsetAsync(v.L.DK, 0, v.bytesK, s), "memset");
+    for (int a = 0; a < d; ++a) {
+      TRY(alloc(&v.tabB[a], es * p * v.Qpad[a], "tables"));
+      TRY(alloc(&v.tabD[a], es * p * v.Qpad[a], "tables"));
+      TRY_CUDA(launch_pad_tables(p, K[a], v.Qpad[a], h->tabB[a], v.tabB[a], v.L.is_fp32, s), "pad tables");
+      TRY_CUDA(launch_pad_tables(p, K[a], v.Qpad[a], h->tabD[a], v.tabD[a], v.L.is_fp32, s), "pad tables");
+    }
+    v.vpart_bytes = (size_t)v.ntiles * vol * es;
+    TRY(alloc(&v.vpart, v.vpart_bytes, "workspace"));
+    TRY(alloc(&v.u_stage, (size_t)h->Ntot * es, "staging"));
+    TRY(alloc(&v.v_stage, (size_t)h->Ntot * es, "staging"));
+    TRY_CUDA(v.k.prepare(), "kernel attributes");
+    g.out[g.nout++] = v.L;
+  }
+  // geometry factors
+  double *ctrl_d = nullptr, *coef_d = nullptr;
+  unsigned int *bad_d = nullptr;
+  TRY(alloc((void **)&ctrl_d, sizeof(double) * h->Ntot * d, "control points"));
+  auto cleanup_tmp = [&]() {
+    cudaFree(ctrl_d);
+    cudaFree(coef_d);
+    cudaFree(bad_d);
+  };
+  cudaError_t ce = cudaMemcpy(ctrl_d, ctrl, sizeof(double) * h->Ntot * d, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess && c.kind == IGASF_COEF_VALUES) {
+    ce = cudaMalloc((void **)&coef_d, sizeof(double) * h->Qtot);
+    if (ce == cudaSuccess) ce = cudaMemcpy(coef_d, c.values, sizeof(double) * h->Qtot, cudaMemcpyHostToDevice);
+  }
+  if (ce == cudaSuccess) ce = cudaMalloc((void **)&bad_d, sizeof(unsigned int));
+  if (ce == cudaSuccess) ce = cudaMemset(bad_d, 0, sizeof(unsigned int));
+  if (ce != cudaSuccess) {
+    cleanup_tmp();
+    int rc = cuda_fail(ce, "geometry inputs");
+    free_plan(h);
+    return rc;
+  }
+  g.d = d;
+  g.p = p;
+  for (int a = 0; a < kMaxDim; ++a) {
+    g.N[a] = h->N[a];
+    g.K[a] = h->K[a];
+    g.tabB[a] = h->tabB[a];
+    g.tabD[a] = h->tabD[a];
+    g.wq[a] = h->weights[a];
+  }
+  g.ctrl = ctrl_d;
+  g.coef_kind = c.kind;
+  g.coef_const = c.constant;
+  g.coef_alpha = c.alpha;
+  g.coef_values = coef_d;
+  g.bad_det = bad_d;
+  ce = launch_geometry(g, s);
+  if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+  unsigned int bad = 0;
+  if (ce == cudaSuccess) ce = cudaMemcpy(&bad, bad_d, sizeof(bad), cudaMemcpyDeviceToHost);
+  cleanup_tmp();
+  if (ce != cudaSuccess) {
+    int rc = cuda_fail(ce, "geometry kernel");
+    free_plan(h);
+    return rc;
+  }
+  if (bad) {
+    free_plan(h);
+    return fail(IGASF_ERR_GEOMETRY, "det J <= 0 at some quadrature point: G is not orientation preserving");
+  }
+  *out = h;
+  return IGASF_OK;
+}
+
+int igasf_apply_prec(igasf_handle h, int op, int prec, const void *u, void *v, void *stream) {
+  if (!h) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL");
+  if (op != IGASF_MASS && op != IGASF_STIFFNESS) return fail(IGASF_ERR_INVALID_ARG, "op = %d", op);
+  if (prec < 0 || prec >= kNumPrec) return fail(IGASF_ERR_INVALID_ARG, "prec = %d", prec);
+  Variant &var = h->var[prec];
+  if (!var.present) return fail(IGASF_ERR_UNSUPPORTED, "precision %d was not stored at setup", prec);
+  if (!u || !v) return fail(IGASF_ERR_INVALID_ARG, "u and v must be non-NULL");
+  const size_t es = prec_size(prec);
+  if (((uintptr_t)u % es) || ((uintptr_t)v % es))
+    return fail(IGASF_ERR_INVALID_ARG, "u and v must be aligned to %zu bytes", es);
+  const uintptr_t ub = (uintptr_t)u, vb = (uintptr_t)v, len = (uintptr_t)h->Ntot * es;
+  if (ub < vb + len && vb < ub + len) return fail(IGASF_ERR_INVALID_ARG, "u and v overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ApplyParams prm;
+  memset(&prm, 0, sizeof(prm));
+  prm.u = u;
+  prm.vpart = var.vpart;
+  prm.D = op == IGASF_MASS ? var.L.DM : var.L.DK;
+  for (int a = 0; a < kMaxDim; ++a) {
+    prm.tabB[a] = var.tabB[a];
+    prm.tabD[a] = var.tabD[a];
+    prm.N[a] = h->N[a];
+    prm.K[a] = h->K[a];
+    prm.T[a] = var.T[a];
+    prm.Qpad[a] = var.Qpad[a];
+  }
+  prm.ntiles = var.ntiles;
+  cudaEvent_t *ev = nullptr;
+  if ((size_t)(h->prof_next + 1) * 3 <= h->prof_events.size()) {
+    ev = &h->prof_events[(size_t)h->prof_next * 3];
+    ++h->prof_next;
+    cudaEventRecord(ev[0], s);
+  }
+  cudaError_t e = var.k.launch[op](prm, s);
+  if (e != cudaSuccess) return cuda_fail(e, "apply kernel launch");
+  if (ev) cudaEventRecord(ev[1], s);
+  e = launch_gather(h->d, prec == IGASF_FP32, var.vpart, v, h->N, var.T, var.k.S, h->p, s);
+  if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
+  if (ev) cudaEventRecord(ev[2], s);
+  return IGASF_OK;
+}
+
+int igasf_apply(igasf_handle h, int op, const void *u, void *v, void *stream) {
+  if (!h) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL");
+  return igasf_apply_prec(h, op, h->default_prec, u, v, stream);
+}
+
+int igasf_apply_host(igasf_handle h, int op, int prec, const void *u_host, void *v_host,
+                     void *stream) {
+  if (!h) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL");
+  if (prec < 0 || prec >= kNumPrec || !h->var[prec].present)
+    return fail(IGASF_ERR_UNSUPPORTED, "precision %d was not stored at setup", prec);
+  if (!u_host || !v_host) return fail(IGASF_ERR_INVALID_ARG, "u and v must be non-NULL");
+  Variant &var = h->var[prec];
+  const size_t bytes = (size_t)h->Ntot * prec_size(prec);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(var.u_stage, u_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy u to the device");
+  int rc = igasf_apply_prec(h, op, prec, var.u_stage, var.v_stage, stream);
+  if (rc != IGASF_OK) return rc;
+  e = cudaMemcpyAsync(v_host, var.v_stage, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy v to the host");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return IGASF_OK;
+}
+
+int igasf_destroy(igasf_handle h) {
+  if (!h) return IGASF_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  free_plan(h);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize before destroy");
+  return IGASF_OK;
+}
+
+int igasf_profile_begin(igasf_handle h, int max_applies) {
+  if (!h || max_applies < 1) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL or max_applies < 1");
+  destroy_events(h);
+  try {
+    h->prof_events.reserve((size_t)max_applies * 3);
+  } catch (...) {
+    return fail(IGASF_ERR_OOM, "host allocation");
+  }
+  for (int i = 0; i < max_applies * 3; ++i) {
+    cudaEvent_t e;
+    cudaError_t ce = cudaEventCreate(&e);
+    if (ce != cudaSuccess) {
+      destroy_events(h);
+      return cuda_fail(ce, "cudaEventCreate");
+    }
+    h->prof_events.push_back(e);
+  }
+  return IGASF_OK;
+}
+
+int igasf_profile_end(igasf_handle h, double *ms, int *applies) {
+  if (!h || !ms) return fail(IGASF_ERR_INVALID_ARG, "handle or ms is NULL");
+  double sum[2] = {0.0, 0.0};
+  const int n = h->prof_next;
+  for (int i = 0; i < n; ++i) {
+    cudaEvent_t *ev = &h->prof_events[(size_t)i * 3];
+    cudaError_t ce = cudaEventSynchronize(ev[2]);
+    float a = 0.f, b = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&a, ev[0], ev[1]);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&b, ev[1], ev[2]);
+    if (ce != cudaSuccess) {
+      destroy_events(h);
+      return cuda_fail(ce, "profile events");
+    }
+    sum[0] += a;
+    sum[1] += b;
+  }
+  ms[0] = sum[0];
+  ms[1] = sum[1];
+  if (applies) *applies = n;
+  destroy_events(h);
+  return IGASF_OK;
+}
+
+int64_t igasf_num_dofs(igasf_handle h) { return h ? h->Ntot : -1; }
+
+int64_t igasf_num_quad_points(igasf_handle h) { return h ? h->Qtot : -1; }
+
+int igasf_describe(igasf_handle h, int prec, igasf_plan_desc *out) {
+  if (!h || !out) return fail(IGASF_ERR_INVALID_ARG, "handle or out is NULL");
+  if (prec < 0 || prec >= kNumPrec || !h->var[prec].present)
+    return fail(IGASF_ERR_UNSUPPORTED, "precision %d was not stored at setup", prec);
+  const Variant &v = h->var[prec];
+  memset(out, 0, sizeof(*out));
+  out->d = h->d;
+  out->order = h->p;
+  for (int a = 0; a < kMaxDim; ++a) {
+    out->tile[a] = a < h->d ? v.k.S[a] : 1;
+    out->tiles[a] = v.T[a];
+  }
+  out->threads_per_block = v.k.threads;
+  out->num_dofs = h->Ntot;
+  out->num_quad_points = h->Qtot;
+  out->factor_bytes[IGASF_MASS] = (int64_t)v.bytesM;
+  out->factor_bytes[IGASF_STIFFNESS] = (int64_t)v.bytesK;
+  out->workspace_bytes = (int64_t)v.vpart_bytes;
+  out->smem_bytes[0] = v.k.smem[0];
+  out->smem_bytes[1] = v.k.smem[1];
+  return IGASF_OK;
+}
+
+int igasf_get_tables(igasf_handle h, int dir, double *nodes, double *weights, double *B,
+                     double *dB) {
+  if (!h) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL");
+  if (dir < 0 || dir >= h->d) return fail(IGASF_ERR_INVALID_ARG, "dir = %d", dir);
+  const int Q = h->Q[dir], p = h->p;
+  cudaError_t e = cudaSuccess;
+  if (nodes) e = cudaMemcpy(nodes, h->nodes[dir], sizeof(double) * Q, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && weights)
+    e = cudaMemcpy(weights, h->weights[dir], sizeof(double) * Q, cudaMemcpyDeviceToHost);
+  std::vector<double> tmp;
+  if (e == cudaSuccess && (B || dB)) tmp.resize((size_t)Q * p);
+  for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+    double *dst = which ? dB : B;
+    if (!dst) continue;
+    e = cudaMemcpy(tmp.data(), which ? h->tabD[dir] : h->tabB[dir], sizeof(double) * Q * p,
+                   cudaMemcpyDeviceToHost);
+    for (int q = 0; q < Q && e == cudaSuccess; ++q)
+      for (int j = 0; j < p; ++j) dst[(size_t)q * p + j] = tmp[(size_t)j * Q + q];
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "copy tables");
+  return IGASF_OK;
+}
+
+int igasf_get_factors(igasf_handle h, int op, int prec, double *out) {
+  if (!h || !out) return fail(IGASF_ERR_INVALID_ARG, "handle or out is NULL");
+  if (op != IGASF_MASS && op != IGASF_STIFFNESS) return fail(IGASF_ERR_INVALID_ARG, "op = %d", op);
+  if (prec < 0 || prec >= kNumPrec || !h->var[prec].present)
+    return fail(IGASF_ERR_UNSUPPORTED, "precision %d was not stored at setup", prec);
+  const int nf = num_fields(h->d, op);
+  const size_t bytes = sizeof(double) * (size_t)h->Qtot * nf;
+  double *tmp = nullptr;
+  cudaError_t e = cudaMalloc((void **)&tmp, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "export buffer");
+  e = launch_export_factors(h->var[prec].L, op, h->Qtot, h->Q, tmp, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out, tmp, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "export factors");
+  return IGASF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// Internal declarations shared by the CUDA translation units of libigasf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "igasf.h"
+
+namespace igasf {
+
+constexpr int kMaxDim = 3;
+constexpr int kNumPrec = 2;        // FP64, FP32
+constexpr int kFieldsK3 = 6;       // 11 12 13 22 23 33
+constexpr int kFieldsK2 = 3;       // 11 12 22
+
+inline int num_fields(int d, int op) { return op == IGASF_MASS ? 1 : (d == 3 ? kFieldsK3 : kFieldsK2); }
+
+// Arguments of one apply launch; pointers are device addresses in the
+// precision of the kernel (float or double).
+struct ApplyParams {
+  const void *u;
+  void *vpart;                // per-tile partial v, [tile][E_d]..[E_1]
+  const void *D;              // factors of the op, tile-major (see FactorLayout)
+  const void *tabB[kMaxDim];  // per direction [j][Qpad]: values of active function j
+  const void *tabD[kMaxDim];  // derivatives, same layout
+  int N[kMaxDim];             // dofs per direction
+  int K[kMaxDim];             // elements per direction
+  int T[kMaxDim];             // tiles per direction
+  int Qpad[kMaxDim];          // T * S * p: row stride of the tables
+  int ntiles;
+};
+
+// A compiled apply kernel for one (d, p, precision) and its tile shape.
+struct ApplyKernel {
+  int S[kMaxDim];             // elements per tile
+  int threads;                // block size
+  size_t smem[2];             // dynamic shared memory, [op]
+  int plane;                  // padded pencils per slab (the factor layout's row length)
+  cudaError_t (*launch[2])(const ApplyParams &, cudaStream_t);
+  cudaError_t (*prepare)();   // raise the dynamic shared memory limit once
+};
+
+// Looks up the kernel for (d, p, prec); false if none is built.
+bool find_apply_kernel(int d, int p, int prec, ApplyKernel *out);
+
+// Tile-major layout of the factors: for tile t, slab index s (the quadrature
+// index along the last direction inside the tile) and field f, a contiguous
+// row of `plane` entries indexed by the pencil (the lexicographic quadrature
+// index over the other directions inside the tile), zero padded.
+struct FactorLayout {
+  int d, p;
+  int S[kMaxDim];
+  int T[kMaxDim];
+  int plane;
+  int is_fp32;
+  void *DM;                   // mass factors (1 field)
+  void *DK;                   // stiffness factors (num_fields)
+};
+
+struct GeometryParams {
+  int d, p;
+  int N[kMaxDim], K[kMaxDim];
+  const double *ctrl;                 // N x d
+  const double *tabB[kMaxDim];        // FP64 [j][K*p]
+  const double *tabD[kMaxDim];
+  const double *wq[kMaxDim];          // [K*p]
+  int coef_kind;
+  double coef_const, coef_alpha;
+  const double *coef_values;          // device, lexicographic quadrature order
+  int nout;
+  FactorLayout out[kNumPrec];
+  unsigned int *bad_det;              // set to 1 if det J <= 0 somewhere
+  double *min_det;                    // unused if NULL
+};
+
+// setup kernels (setup.cu)
+cudaError_t launch_tables(int p, int K, const double *knots, const int *span, double *nodes,
+                          double *weights, double *tabB, double *tabD, cudaStream_t s);
+cudaError_t launch_geometry(const GeometryParams &g, cudaStream_t s);
+cudaError_t launch_pad_tables(int p, int K, int Qpad, const double *src, void *dst, int is_fp32,
+                              cudaStream_t s);
+cudaError_t launch_export_factors(const FactorLayout &L, int op, int64_t Qtot, const int *Q,
+                                  double *out, cudaStream_t s);
+cudaError_t launch_gather(int d, int is_fp32, const void *vpart, void *v, const int *N,
+                          const int *T, const int *S, int p, cudaStream_t s);
+
+}  // namespace igasf

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libigasf (include/igasf.h).
+
+Argument marshalling only: every step of setup and apply runs in the CUDA
+library. PyTorch supplies device memory and streams. There is no fallback:
+if the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libigasf.so")
+
+OK = 0
+MASS = 0
+STIFFNESS = 1
+FP64 = 0
+FP32 = 1
+COEF_CONSTANT = 0
+COEF_EXP_SIN_COS = 1
+COEF_VALUES = 2
+
+ERRORS = {
+    -1: "INVALID_ARG", -2: "KNOTS", -3: "GEOMETRY", -4: "UNSUPPORTED", -5: "CUDA",
+    -6: "OOM", -7: "TIMEOUT",
+}
+
+# every symbol include/igasf.h declares
+EXPORTED = [
+    "igasf_setup", "igasf_apply", "igasf_apply_prec", "igasf_apply_host", "igasf_destroy",
+    "igasf_num_dofs", "igasf_num_quad_points", "igasf_describe", "igasf_get_tables",
+    "igasf_get_factors", "igasf_profile_begin", "igasf_profile_end",
+    "igasf_last_error_message", "igasf_version",
+]
+
+
+class IgasfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("igasf error %d (%s): %s" % (code, ERRORS.get(code, "?"), msg))
+        self.code = code
+
+
+class Coef(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("constant", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("values", ctypes.POINTER(ctypes.c_double))]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precisions", ctypes.c_uint), ("default_prec", ctypes.c_int),
+                ("tile", ctypes.c_int * 3), ("reserved", ctypes.c_int * 8)]
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("order", ctypes.c_int), ("tile", ctypes.c_int * 3),
+                ("tiles", ctypes.c_int * 3), ("threads_per_block", ctypes.c_int),
+                ("num_dofs", ctypes.c_int64), ("num_quad_points", ctypes.c_int64),
+                ("factor_bytes", ctypes.c_int64 * 2), ("workspace_bytes", ctypes.c_int64),
+                ("smem_bytes", ctypes.c_size_t * 2)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libigasf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libigasf.so not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.igasf_setup.argtypes = [ctypes.c_int, ip, ip, ctypes.POINTER(dp), dp,
+                                ctypes.POINTER(Coef), ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    lib.igasf_apply.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.igasf_apply_prec.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+    lib.igasf_apply_host.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+    lib.igasf_destroy.argtypes = [vp]
+    lib.igasf_num_dofs.argtypes = [vp]
+    lib.igasf_num_dofs.restype = ctypes.c_int64
+    lib.igasf_num_quad_points.argtypes = [vp]
+    lib.igasf_num_quad_points.restype = ctypes.c_int64
+    lib.igasf_describe.argtypes = [vp, ctypes.c_int, ctypes.POINTER(PlanDesc)]
+    lib.igasf_get_tables.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp]
+    lib.igasf_get_factors.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
+    lib.igasf_profile_begin.argtypes = [vp, ctypes.c_int]
+    lib.igasf_profile_end.argtypes = [vp, dp, ip]
+    lib.igasf_last_error_message.restype = ctypes.c_char_p
+    lib.igasf_version.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        msg = load_library().igasf_last_error_message().decode(errors="replace")
+        raise IgasfError(rc, msg)
+
+
+def _dptr(a: Optional[np.ndarray]):
+    dp = ctypes.POINTER(ctypes.c_double)
+    return a.ctypes.data_as(dp) if a is not None else ctypes.cast(None, dp)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """A setup handle: igasf_setup on construction, igasf_destroy on close()."""
+
+    def __init__(self, d: int, orders: Sequence[int], knots: Sequence[np.ndarray],
+                 ctrl: np.ndarray, coef_kind: int = COEF_CONSTANT, coef_constant: float = 1.0,
+                 coef_alpha: float = 0.0, coef_values: Optional[np.ndarray] = None,
+                 precisions: Sequence[int] = (FP64,), default_prec: Optional[int] = None,
+                 tile: Optional[Sequence[int]] = None):
+        lib = load_library()
+        self.d = d
+        self._orders = (ctypes.c_int * d)(*orders)
+        self._knots = [np.ascontiguousarray(t, dtype=np.float64) for t in knots]
+        self._lens = (ctypes.c_int * d)(*[len(t) for t in self._knots])
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._kptrs = (dp * d)(*[_dptr(t) for t in self._knots])
+        self._ctrl = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1)
+        self._coef_values = None if coef_values is None else \
+            np.ascontiguousarray(coef_values, dtype=np.float64)
+        coef = Coef(coef_kind, coef_constant, coef_alpha, _dptr(self._coef_values))
+        opt = Options()
+        bits = 0
+        for p in precisions:
+            bits |= 1 << int(p)
+        opt.precisions = bits
+        opt.default_prec = int(precisions[0] if default_prec is None else default_prec)
+        if tile is not None:
+            for i, s in enumerate(tile):
+                opt.tile[i] = int(s)
+        h = ctypes.c_void_p()
+        _check(lib.igasf_setup(d, self._orders, self._lens, self._kptrs, _dptr(self._ctrl),
+                               ctypes.byref(coef), ctypes.byref(opt), ctypes.byref(h)))
+        self.handle = h
+        self.precisions = tuple(int(p) for p in precisions)
+        self.num_dofs = int(lib.igasf_num_dofs(h))
+        self.num_quad_points = int(lib.igasf_num_quad_points(h))
+
+    @classmethod
+    def from_patch(cls, patch, **kw):
+        return cls(patch.d, patch.orders, patch.knots, patch.ctrl, coef_kind=patch.coef_kind,
+                   coef_constant=patch.coef_constant, coef_alpha=patch.coef_alpha,
+                   coef_values=patch.coef_values, **kw)
+
+    def _h(self):
+        if self.handle is None:
+            raise RuntimeError("plan is closed")
+        return self.handle
+
+    def apply(self, op: int, u, v, prec: int = FP64, stream=None):
+        """v = A u on device tensors (float64 for FP64, float32 for FP32)."""
+        _check(load_library().igasf_apply_prec(self._h(), int(op), int(prec), u.data_ptr(),
+                                               v.data_ptr(), _stream_handle(stream)))
+        return v
+
+    def apply_default(self, op: int, u, v, stream=None):
+        _check(load_library().igasf_apply(self._h(), int(op), u.data_ptr(), v.data_ptr(),
+                                          _stream_handle(stream)))
+        return v
+
+    def apply_host(self, op: int, u, v, prec: int = FP64, stream=None):
+        """v = A u with host arrays (numpy or pinned CPU tensors); synchronous."""
+        up = u.ctypes.data if isinstance(u, np.ndarray) else u.data_ptr()
+        vp = v.ctypes.data if isinstance(v, np.ndarray) else v.data_ptr()
+        _check(load_library().igasf_apply_host(self._h(), int(op), int(prec), up, vp,
+                                               _stream_handle(stream)))
+        return v
+
+    def describe(self, prec: int = FP64) -> dict:
+        d = PlanDesc()
+        _check(load_library().igasf_describe(self._h(), int(prec), ctypes.byref(d)))
+        return dict(d=d.d, order=d.order, tile=list(d.tile), tiles=list(d.tiles),
+                    threads_per_block=d.threads_per_block, num_dofs=d.num_dofs,
+                    num_quad_points=d.num_quad_points,
+                    factor_bytes=[int(x) for x in d.factor_bytes],
+                    workspace_bytes=int(d.workspace_bytes),
+                    smem_bytes=[int(x) for x in d.smem_bytes])
+
+    def tables(self, direction: int):
+        """(nodes, weights, B[Q, p], dB[Q, p]) of one direction, FP64 from the device."""
+        desc = self.describe(self.precisions[0])
+        p = desc["order"]
+        # Q of this direction from the knot vector: simple knots, K = nk - 2p + 1
+        Q = (len(self._knots[direction]) - 2 * p + 1) * p
+        nodes, weights = np.zeros(Q), np.zeros(Q)
+        B, dB = np.zeros((Q, p)), np.zeros((Q, p))
+        _check(load_library().igasf_get_tables(self._h(), direction, _dptr(nodes), _dptr(weights),
+                                               _dptr(B), _dptr(dB)))
+        return nodes, weights, B, dB
+
+    def factors(self, op: int, prec: int = FP64) -> np.ndarray:
+        nf = 1 if op == MASS else self.d * (self.d + 1) // 2
+        out = np.zeros(self.num_quad_points * nf)
+        _check(load_library().igasf_get_factors(self._h(), int(op), int(prec), _dptr(out)))
+        return out.reshape(self.num_quad_points, nf) if nf > 1 else out
+
+    def profile_begin(self, max_applies: int):
+        _check(load_library().igasf_profile_begin(self._h(), int(max_applies)))
+
+    def profile_end(self):
+        """Summed (tile kernel ms, gather ms) and the number of applies timed."""
+        ms = np.zeros(2)
+        n = ctypes.c_int(0)
+        _check(load_library().igasf_profile_end(self._h(), _dptr(ms), ctypes.byref(n)))
+        return float(ms[0]), float(ms[1]), int(n.value)
+
+    def close(self):
+        if self.handle is not None:
+            _check(load_library().igasf_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,66 @@
+"""Shared helpers of the GPU tests: run the CUDA path through the C-ABI binding
+and the oracle on the same seeded inputs."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+from paper_1809_05471_gb300 import igasf as G
+from paper_1809_05471_gb300 import inputs as I
+
+TOL = {G.FP64: 1e-12, G.FP32: 1e-5}
+DTYPE = {G.FP64: "float64", G.FP32: "float32"}
+
+
+def gpu_apply(plan, op, u, prec):
+    import torch
+    dt = getattr(torch, DTYPE[prec])
+    ud = torch.as_tensor(np.asarray(u), device="cuda").to(dt)
+    vd = torch.empty_like(ud)
+    plan.apply(op, ud, vd, prec=prec)
+    torch.cuda.synchronize()
+    return vd.double().cpu().numpy()
+
+
+def oracle_full(patch, op, u, mode="elementwise"):
+    """Whole v = A u and ||A||_inf from the oracle."""
+    if mode == "csr":
+        rp, ci, va = O.assemble_csr(patch, op)
+        return O.spmv(rp, ci, va, u), O.csr_inf_norm(rp, va)
+    rows = np.arange(patch.num_dofs)
+    v, ra = O.apply_rows(patch, op, u, rows)
+    return v, float(ra.max())
+
+
+def sample_rows(patch, n, seed=0):
+    """Rows on corners, edges and faces of the dof grid plus random interior ones."""
+    Ns = patch.dofs_per_dir
+    d = patch.d
+    rng = np.random.default_rng(seed)
+    picks = set()
+    for corner in range(2 ** d):
+        idx = [(Ns[a] - 1) if (corner >> a) & 1 else 0 for a in range(d)]
+        picks.add(tuple(idx))
+    while len(picks) < n:
+        idx = []
+        for a in range(d):
+            r = rng.random()
+            if r < 0.15:
+                idx.append(int(rng.integers(0, min(Ns[a], 3))))
+            elif r < 0.3:
+                idx.append(int(Ns[a] - 1 - rng.integers(0, min(Ns[a], 3))))
+            else:
+                idx.append(int(rng.integers(0, Ns[a])))
+        picks.add(tuple(idx))
+    rows = []
+    for idx in sorted(picks):
+        lin, s = 0, 1
+        for a in range(d):
+            lin += s * idx[a]
+            s *= Ns[a]
+        rows.append(lin)
+    return np.array(sorted(rows), dtype=np.int64)
+
+
+def scaled_err(v, v_ref, a_inf, u):
+    return I.scaled_error(v, v_ref, a_inf, u)

@@ -1,0 +1,158 @@
+"""The C-ABI library builds, loads and exports what include/igasf.h declares;
+host-side validation rejects bad inputs before any CUDA call (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1809_05471_gb300 import igasf as G
+from paper_1809_05471_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "igasf.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w \*]*?\b(igasf_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1809_05471_gb300 import build
+    build.build()
+    return G.load_library()
+
+
+def test_header_declares_the_binding_list():
+    assert _declared_functions() == sorted(G.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", G.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (igasf_\w+)", out))
+    for name in _declared_functions():
+        assert name in exported, name
+        assert hasattr(lib, name)
+
+
+def test_version(lib):
+    assert lib.igasf_version() == 1
+
+
+def _setup(lib, d, orders, knots, ctrl, coef=None, opt=None):
+    orders_c = (ctypes.c_int * d)(*orders)
+    knots = [np.ascontiguousarray(t, dtype=np.float64) for t in knots]
+    lens = (ctypes.c_int * d)(*[len(t) for t in knots])
+    dp = ctypes.POINTER(ctypes.c_double)
+    kp = (dp * d)(*[t.ctypes.data_as(dp) for t in knots])
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float64)
+    h = ctypes.c_void_p()
+    rc = lib.igasf_setup(d, orders_c, lens, kp, ctrl.ctypes.data_as(dp),
+                         ctypes.byref(coef) if coef is not None else None,
+                         ctypes.byref(opt) if opt is not None else None, ctypes.byref(h))
+    return rc, h
+
+
+def _patch(d=3, p=3, K=2):
+    patch, _ = I.make_patch(d, p, K)
+    return patch
+
+
+def test_rejects_bad_dimension_and_orders(lib):
+    pt = _patch()
+    rc, h = _setup(lib, 4, [3] * 4, pt.knots + [pt.knots[0]], pt.ctrl)
+    assert rc == -4 and h.value is None
+    rc, _ = _setup(lib, 3, [3, 3, 4], pt.knots, pt.ctrl)
+    assert rc == -4
+    assert b"orders differ" in lib.igasf_last_error_message()
+    rc, _ = _setup(lib, 3, [0, 0, 0], pt.knots, pt.ctrl)
+    assert rc == -1
+    big = I.make_patch(3, 10, 1)[0]
+    rc, _ = _setup(lib, 3, [10] * 3, big.knots, big.ctrl)
+    assert rc == -4
+
+
+def test_rejects_bad_knots(lib):
+    pt = _patch()
+    t = pt.knots[0].copy()
+    dec = t.copy()
+    dec[3], dec[4] = dec[4], dec[3] + 0.5
+    rc, _ = _setup(lib, 3, [3] * 3, [dec, t, t], pt.ctrl)
+    assert rc == -2
+    not_open = t.copy()
+    not_open[1] = 0.01
+    rc, _ = _setup(lib, 3, [3] * 3, [not_open, t, t], pt.ctrl)
+    assert rc == -2
+    rc, _ = _setup(lib, 3, [3] * 3, [t[:4], t, t], pt.ctrl)
+    assert rc == -2
+    nan = t.copy()
+    nan[3] = np.nan
+    rc, _ = _setup(lib, 3, [3] * 3, [nan, t, t], pt.ctrl)
+    assert rc == -2
+    # interior multiplicity == order: not an open knot vector of this order
+    full = I.open_knots_from_breaks(3, [0, 0.5, 1], [3])
+    rc, _ = _setup(lib, 3, [3] * 3, [full, t, t], pt.ctrl)
+    assert rc == -2
+    # repeated interior knot below the order: valid, but not on the GPU path
+    rep = I.open_knots_from_breaks(3, [0, 0.5, 1], [2])
+    rc, _ = _setup(lib, 3, [3] * 3, [rep, t, t], pt.ctrl)
+    assert rc == -4
+    assert b"repeated interior knot" in lib.igasf_last_error_message()
+
+
+def test_rejects_null_and_bad_options(lib):
+    pt = _patch()
+    h = ctypes.c_void_p()
+    assert lib.igasf_setup(3, None, None, None, None, None, None, ctypes.byref(h)) == -1
+    assert lib.igasf_setup(3, None, None, None, None, None, None, None) == -1
+    opt = G.Options()
+    opt.reserved[0] = 1
+    rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, opt=opt)
+    assert rc == -1
+    opt = G.Options()
+    opt.default_prec = 7
+    rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, opt=opt)
+    assert rc == -1
+    opt = G.Options()
+    opt.precisions = 1 << 5
+    rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, opt=opt)
+    assert rc == -1
+    opt = G.Options()
+    opt.tile[0] = 3          # not a built tile shape
+    rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, opt=opt)
+    assert rc == -4
+    coef = G.Coef(G.COEF_VALUES, 0.0, 0.0, ctypes.cast(None, ctypes.POINTER(ctypes.c_double)))
+    rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, coef=coef)
+    assert rc == -1
+    coef = G.Coef(9, 0.0, 0.0, ctypes.cast(None, ctypes.POINTER(ctypes.c_double)))
+    rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, coef=coef)
+    assert rc == -1
+
+
+def test_null_handle_calls(lib):
+    assert lib.igasf_apply(None, 0, None, None, None) == -1
+    assert lib.igasf_apply_prec(None, 0, 0, None, None, None) == -1
+    assert lib.igasf_apply_host(None, 0, 0, None, None, None) == -1
+    assert lib.igasf_destroy(None) == 0
+    assert lib.igasf_num_dofs(None) == -1
+    assert lib.igasf_num_quad_points(None) == -1
+    assert lib.igasf_describe(None, 0, None) == -1
+    assert lib.igasf_get_tables(None, 0, None, None, None, None) == -1
+    assert lib.igasf_get_factors(None, 0, 0, None) == -1
+
+
+def test_binding_raises_without_library(tmp_path):
+    import importlib
+    mod = importlib.reload(G)
+    try:
+        mod._lib = None
+        with pytest.raises(RuntimeError, match="not built"):
+            mod.load_library(str(tmp_path / "missing.so"))
+    finally:
+        importlib.reload(G)

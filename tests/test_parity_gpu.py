@@ -1,0 +1,278 @@
+"""CUDA path vs the FP64 oracle, through the C-ABI (GPU).
+
+Every test builds the same seeded inputs for both sides. Tolerances (scaled
+max-norm error ||v - v_ref||_inf / (||A||_inf ||u||_inf)):
+  FP64: 1e-12 (the exactness of sum factorization, Sec. 1 and Sec. 8: the
+        factorized apply equals the assembled quadrature operator up to rounding);
+  FP32: 1e-5  (FP32 factors, tables and arithmetic; unit roundoff 6e-8 times
+        the ~6p+9 terms of the longest accumulation chain, with margin).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1809_05471_gb300 import igasf as G
+from paper_1809_05471_gb300 import inputs as I
+from tests.gpu_helpers import TOL, gpu_apply, oracle_full, sample_rows, scaled_err
+
+pytestmark = pytest.mark.gpu
+
+_CACHE = {}
+
+
+def _oracle_cached(key, fn):
+    if key not in _CACHE:
+        _CACHE[key] = fn()
+    return _CACHE[key]
+
+
+def _nonuniform_knots(p, K, seed):
+    rng = np.random.default_rng(seed)
+    h = rng.uniform(0.5, 1.5, K)
+    br = np.concatenate([[0.0], np.cumsum(h) / h.sum()])
+    return I.open_knots_from_breaks(p, br)
+
+
+# --- row a1: univariate tables ------------------------------------------------
+
+@pytest.mark.parametrize("p", range(2, 10))
+def test_tables_match_oracle(p):
+    K = (5, 3, 4)
+    knots = [_nonuniform_knots(p, k, 10 + a) for a, k in enumerate(K)]
+    patch, _ = I.make_patch(3, p, list(K), knots=knots)
+    with G.Plan.from_patch(patch, precisions=(G.FP64,)) as plan:
+        for a in range(3):
+            nodes, weights, B, dB = plan.tables(a)
+            xq, wq, Bo, dBo = O.tables_1d(knots[a], p)
+            assert np.max(np.abs(nodes - xq)) < 1e-15
+            assert np.max(np.abs(weights - wq)) < 1e-15
+            Q = len(xq)
+            e = np.arange(Q) // p
+            for j in range(p):
+                assert np.max(np.abs(B[:, j] - Bo[np.arange(Q), e + j])) < 1e-14
+                scale = np.max(np.abs(dBo))
+                assert np.max(np.abs(dB[:, j] - dBo[np.arange(Q), e + j])) < 1e-13 * scale
+
+
+# --- row a2: geometry factors ------------------------------------------------
+
+@pytest.mark.parametrize("d,p,K", [(3, 2, (9, 5, 4)), (3, 4, (5, 6, 3)), (3, 7, (3, 2, 3)),
+                                   (3, 9, (2, 3, 2)), (2, 3, (17, 9)), (2, 6, (9, 4))])
+def test_factors_match_oracle(d, p, K):
+    knots = [_nonuniform_knots(p, k, 20 + a) for a, k in enumerate(K)]
+    patch, _ = I.make_patch(d, p, list(K), noise_amp=0.2 / max(K), seed=3, knots=knots,
+                            coef_kind=I.COEF_EXP_SIN_COS, coef_alpha=0.5)
+    qd = O.quad_data(patch)
+    w = qd["w"]
+    fm = w * qd["FM"]
+    iu = np.triu_indices(d)
+    fk = (w[:, None, None] * qd["FK"])[:, iu[0], iu[1]]
+    with G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32)) as plan:
+        m64 = plan.factors(G.MASS, G.FP64)
+        k64 = plan.factors(G.STIFFNESS, G.FP64)
+        assert np.max(np.abs(m64 - fm)) < 1e-13 * np.max(np.abs(fm))
+        assert np.max(np.abs(k64 - fk)) < 1e-12 * np.max(np.abs(fk))
+        m32 = plan.factors(G.MASS, G.FP32)
+        k32 = plan.factors(G.STIFFNESS, G.FP32)
+        assert np.max(np.abs(m32 - fm) / np.abs(fm)) < 1e-7       # one FP32 rounding
+        assert np.max(np.abs(k32 - fk)) < 1e-7 * np.max(np.abs(fk))
+
+
+def test_factor_values_per_quad_point_coefficient():
+    patch, _ = I.make_patch(3, 3, [4, 3, 5], noise_amp=0.02, seed=8)
+    rng = np.random.default_rng(1)
+    patch.coef_kind = I.COEF_VALUES
+    patch.coef_values = rng.uniform(0.5, 2.0, patch.num_quad_points)
+    qd = O.quad_data(patch)
+    iu = np.triu_indices(3)
+    fk = (qd["w"][:, None, None] * qd["FK"])[:, iu[0], iu[1]]
+    with G.Plan.from_patch(patch) as plan:
+        assert np.max(np.abs(plan.factors(G.STIFFNESS) - fk)) < 1e-12 * np.max(np.abs(fk))
+
+
+# --- rows a3-a7: the apply, whole vectors at sizes spanning several tiles ----
+
+FULL_CASES = [
+    # (d, p, K): K spans >= 2 tiles per direction for both precisions, with ragged tails
+    (2, 2, (17, 12)), (2, 3, (16, 16)), (2, 5, (17, 9)), (2, 9, (9, 10)),
+    (3, 2, (17, 9, 10)), (3, 3, (17, 9, 9)), (3, 4, (9, 6, 5)),
+]
+
+
+@pytest.mark.parametrize("d,p,K", FULL_CASES)
+@pytest.mark.parametrize("op", [G.MASS, G.STIFFNESS], ids=["mass", "stiffness"])
+def test_apply_matches_oracle_whole_vector(d, p, K, op):
+    knots = [_nonuniform_knots(p, k, 30 + a) for a, k in enumerate(K)]
+    patch, u = I.make_patch(d, p, list(K), noise_amp=0.2 / max(K), seed=5, knots=knots,
+                            coef_kind=I.COEF_EXP_SIN_COS, coef_alpha=0.5)
+    v_ref, a_inf = _oracle_cached(("full", d, p, K, op), lambda: oracle_full(patch, op, u))
+    with G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32)) as plan:
+        for prec in (G.FP64, G.FP32):
+            v = gpu_apply(plan, op, u, prec)
+            err = scaled_err(v, v_ref, a_inf, u)
+            assert err < TOL[prec], (prec, err)
+
+
+def test_config_small_2d_identity_matches_csr():
+    """d=2, p=3, 16x16 elements, identity geometry, a=1, FP64, u from seed 0."""
+    patch, u = I.config_small_2d()
+    for op in (G.MASS, G.STIFFNESS):
+        v_ref, a_inf = oracle_full(patch, op, u, mode="csr")
+        with G.Plan.from_patch(patch) as plan:
+            v = gpu_apply(plan, op, u, G.FP64)
+        assert scaled_err(v, v_ref, a_inf, u) < 1e-12
+
+
+SAMPLED_CASES = [(5, (9, 9, 5)), (6, (9, 5, 5)), (7, (5, 5, 5)), (8, (5, 5, 3)), (9, (5, 3, 5))]
+
+
+@pytest.mark.parametrize("p,K", SAMPLED_CASES)
+def test_apply_high_order_sampled_rows(p, K):
+    knots = [_nonuniform_knots(p, k, 40 + a) for a, k in enumerate(K)]
+    patch, u = I.make_patch(3, p, list(K), noise_amp=0.2 / max(K), seed=6, knots=knots,
+                            coef_kind=I.COEF_EXP_SIN_COS, coef_alpha=0.5)
+    rows = sample_rows(patch, 48 if p < 8 else 24, seed=p)
+    with G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32)) as plan:
+        for op in (G.MASS, G.STIFFNESS):
+            vr, ra = O.apply_rows(patch, op, u, rows)
+            for prec in (G.FP64, G.FP32):
+                v = gpu_apply(plan, op, u, prec)[rows]
+                assert scaled_err(v, vr, ra.max(), u) < TOL[prec]
+
+
+# --- the benchmark workloads at full size, sampled rows ----------------------
+
+def test_config_cube_64_p4_sampled():
+    """d=3, p=4, 64^3 elements, perturbed cube, a = exp(0.5 sin 2pi x cos 2pi y);
+    FP64 and FP32 applies of K and M on 256 sampled rows."""
+    patch, u = I.config_cube(p=4, K=64)
+    rows = sample_rows(patch, 256, seed=1)
+    with G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32)) as plan:
+        for op in (G.MASS, G.STIFFNESS):
+            vr, ra = O.apply_rows(patch, op, u, rows)
+            for prec in (G.FP64, G.FP32):
+                v = gpu_apply(plan, op, u, prec)[rows]
+                assert scaled_err(v, vr, ra.max(), u) < TOL[prec]
+
+
+@pytest.mark.parametrize("p", range(2, 10))
+def test_order_sweep_2m_dofs_sampled(p):
+    """Order sweep at about 2M dofs (127 - p elements per direction), K apply."""
+    patch, u = I.config_sweep(p)
+    nrows = 16 if p >= 8 else 32
+    rows = sample_rows(patch, nrows, seed=100 + p)
+    vr, ra = O.apply_rows(patch, G.STIFFNESS, u, rows)
+    with G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32)) as plan:
+        for prec in (G.FP64, G.FP32):
+            v = gpu_apply(plan, G.STIFFNESS, u, prec)[rows]
+            assert scaled_err(v, vr, ra.max(), u) < TOL[prec]
+
+
+# --- invariants of the CUDA path alone at full size ---------------------------
+
+def test_invariants_config_cube():
+    import torch
+    patch, u = I.config_cube(p=4, K=64)
+    with G.Plan.from_patch(patch, precisions=(G.FP64,)) as plan:
+        N = plan.num_dofs
+        one = torch.ones(N, dtype=torch.float64, device="cuda")
+        out = torch.empty_like(one)
+        plan.apply(G.STIFFNESS, one, out)
+        k1 = out.abs().max().item()
+        rng = np.random.default_rng(2)
+        a = torch.as_tensor(rng.uniform(-1, 1, N), device="cuda")
+        b = torch.as_tensor(rng.uniform(-1, 1, N), device="cuda")
+        ka, kb = torch.empty_like(a), torch.empty_like(b)
+        plan.apply(G.STIFFNESS, a, ka)
+        plan.apply(G.STIFFNESS, b, kb)
+        sym = abs((b @ ka).item() - (a @ kb).item()) / abs((b @ ka).item())
+        plan.apply(G.MASS, one, out)
+        vol = out.sum().item()
+        fm = plan.factors(G.MASS)
+        ka_max = ka.abs().max().item()
+    # K 1 = 0, K symmetric, 1^T M 1 = sum_x w |det J| = volume of the cube up to quadrature error
+    assert k1 < 1e-12 * ka_max
+    assert sym < 1e-12
+    assert abs(vol - fm.sum()) < 1e-12
+    assert abs(vol - 1.0) < 1e-6
+
+
+# --- edge cases and determinism -----------------------------------------------
+
+@pytest.mark.parametrize("d,p,K", [(3, 2, (1, 1, 1)), (3, 4, (1, 2, 3)), (3, 9, (1, 1, 1)),
+                                   (3, 5, (3, 1, 2)), (2, 7, (1, 1)), (2, 2, (1, 30))])
+def test_tiny_patches_single_partial_tile(d, p, K):
+    patch, u = I.make_patch(d, p, list(K), noise_amp=0.05, seed=12,
+                            coef_kind=I.COEF_EXP_SIN_COS, coef_alpha=0.5)
+    with G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32)) as plan:
+        for op in (G.MASS, G.STIFFNESS):
+            v_ref, a_inf = oracle_full(patch, op, u, mode="csr")
+            for prec in (G.FP64, G.FP32):
+                assert scaled_err(gpu_apply(plan, op, u, prec), v_ref, a_inf, u) < TOL[prec]
+
+
+def test_apply_is_deterministic_and_host_path_matches():
+    import torch
+    patch, u = I.config_cube(p=3, K=20)
+    with G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32)) as plan:
+        for prec, dt, npdt in ((G.FP64, torch.float64, np.float64), (G.FP32, torch.float32, np.float32)):
+            ud = torch.as_tensor(u, device="cuda").to(dt)
+            v1, v2 = torch.empty_like(ud), torch.empty_like(ud)
+            plan.apply(G.STIFFNESS, ud, v1, prec=prec)
+            plan.apply(G.STIFFNESS, ud, v2, prec=prec)
+            torch.cuda.synchronize()
+            assert torch.equal(v1, v2)
+            uh = torch.as_tensor(u.astype(npdt)).pin_memory()
+            vh = torch.empty_like(uh).pin_memory()
+            plan.apply_host(G.STIFFNESS, uh, vh, prec=prec)
+            assert torch.equal(vh, v1.cpu())
+
+
+def test_default_precision_apply():
+    import torch
+    patch, u = I.config_cube(p=2, K=9)
+    with G.Plan.from_patch(patch, precisions=(G.FP32,)) as plan:
+        ud = torch.as_tensor(u, device="cuda").float()
+        v1, v2 = torch.empty_like(ud), torch.empty_like(ud)
+        plan.apply_default(G.STIFFNESS, ud, v1)
+        plan.apply(G.STIFFNESS, ud, v2, prec=G.FP32)
+        torch.cuda.synchronize()
+        assert torch.equal(v1, v2)
+        with pytest.raises(G.IgasfError) as ei:
+            plan.apply(G.STIFFNESS, ud.double(), v1.double(), prec=G.FP64)
+        assert ei.value.code == -4
+
+
+def test_apply_argument_errors():
+    import torch
+    patch, u = I.config_cube(p=2, K=9)
+    with G.Plan.from_patch(patch, precisions=(G.FP64,)) as plan:
+        ud = torch.as_tensor(u, device="cuda")
+        big = torch.zeros(2 * len(u) + 1, dtype=torch.float64, device="cuda")
+        with pytest.raises(G.IgasfError) as ei:      # misaligned
+            plan.apply(G.STIFFNESS, ud, _misaligned(big, len(u)))
+        assert ei.value.code == -1
+        with pytest.raises(G.IgasfError) as ei:      # overlap
+            plan.apply(G.STIFFNESS, big[:len(u)], big[len(u) // 2:len(u) // 2 + len(u)])
+        assert ei.value.code == -1
+        with pytest.raises(G.IgasfError) as ei:      # bad op
+            plan.apply(5, ud, torch.empty_like(ud))
+        assert ei.value.code == -1
+
+
+class _misaligned:
+    """A fake tensor whose data pointer is off by 4 bytes."""
+
+    def __init__(self, base, n):
+        self.base = base
+
+    def data_ptr(self):
+        return self.base.data_ptr() + 4
+
+
+def test_setup_rejects_inverted_geometry():
+    patch, u = I.make_patch(3, 3, 4)
+    patch.ctrl[:, 0] = -patch.ctrl[:, 0]   # mirror: det J < 0 everywhere
+    with pytest.raises(G.IgasfError) as ei:
+        G.Plan.from_patch(patch)
+    assert ei.value.code == -3
