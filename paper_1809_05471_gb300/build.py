@@ -30,8 +30,9 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
+    defs = ["-DIGASF_TILE_SEARCH"] if os.environ.get("IGASF_TILE_SEARCH") else []
     return ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
-            "-I", INCLUDE, "-I", CSRC, *extra]
+            "-I", INCLUDE, "-I", CSRC, *defs, *extra]
 
 
 def _newest_header() -> float:
@@ -54,6 +55,10 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int = 0) -> st
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr = _newest_header()
+    flavour = os.path.join(BUILD, "flavour")
+    want = "tile-search" if os.environ.get("IGASF_TILE_SEARCH") else "default"
+    if os.path.exists(flavour) and open(flavour).read() != want:
+        force = True
     todo = []
     for s in srcs:
         obj = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
@@ -68,6 +73,8 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int = 0) -> st
                 if err.strip():
                     logs.append("== %s\n%s" % (os.path.basename(obj), err))
     objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    with open(flavour, "w") as f:
+        f.write(want)
     if todo or not os.path.exists(LIB):
         tmp = LIB + ".tmp%d" % os.getpid()
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]

@@ -153,7 +153,9 @@ apply3d_kernel(const ApplyParams prm) {
     const int q1 = tid % Q1, q2 = tid / Q1;
     const bool valid = (e01 + q1 / P < prm.K[0]) && (e02 + q2 / P < prm.K[1]);
     const int ke3 = min(S3, prm.K[2] - e03);
-    const T *Dt = static_cast<const T *>(prm.D) + (size_t)tile * Q3 * NF * PL + tid;
+    // layout.h with one pencil per unit: mass [slab][pencil]; stiffness
+    // [slab][chunk c][pencil] with chunks (11,12), (13,22), (23,33) of two values
+    const T *Dt = static_cast<const T *>(prm.D) + (size_t)tile * Q3 * NF * PL + (STIFF ? 2 : 1) * tid;
     T y0[E3], y1[E3], y2[E3], z0[E3], z1[E3], z2[E3];
 #pragma unroll
     for (int n = 0; n < E3; ++n) {
@@ -177,11 +179,11 @@ apply3d_kernel(const ApplyParams prm) {
             T D11 = T(0), D12 = T(0), D13 = T(0), D22 = T(0), D23 = T(0), D33 = T(0);
             if (valid) {
               D11 = ld_stream(Dq);
-              D12 = ld_stream(Dq + PL);
+              D12 = ld_stream(Dq + 1);
               D13 = ld_stream(Dq + 2 * PL);
-              D22 = ld_stream(Dq + 3 * PL);
+              D22 = ld_stream(Dq + 2 * PL + 1);
               D23 = ld_stream(Dq + 4 * PL);
-              D33 = ld_stream(Dq + 5 * PL);
+              D33 = ld_stream(Dq + 4 * PL + 1);
             }
             T d1 = T(0), d2 = T(0), d3 = T(0);
 #pragma unroll
@@ -305,6 +307,7 @@ ApplyKernel make_apply3d() {
   k.smem[IGASF_MASS] = G::smem_words(false) * sizeof(T);
   k.smem[IGASF_STIFFNESS] = G::smem_words(true) * sizeof(T);
   k.plane = G::PL;
+  k.lanes = 1;
   k.launch[IGASF_MASS] = &launch_apply3d<T, P, S1, S2, S3, false>;
   k.launch[IGASF_STIFFNESS] = &launch_apply3d<T, P, S1, S2, S3, true>;
   k.prepare = &prepare_apply3d<T, P, S1, S2, S3>;

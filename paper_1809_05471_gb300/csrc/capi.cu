@@ -206,20 +206,24 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
   if (c.kind == IGASF_COEF_VALUES && !c.values)
     return fail(IGASF_ERR_INVALID_ARG, "coef.values is NULL");
   int K[kMaxDim] = {1, 1, 1};
+  double ntot = 1.0, qtot = 1.0;
   for (int a = 0; a < d; ++a) {
     int rc = check_knots(a, p, knot_lengths[a], knots[a], &K[a]);
     if (rc != IGASF_OK) return rc;
+    ntot *= knot_lengths[a] - p;
+    qtot *= (double)K[a] * p;
   }
+  if (ntot >= 2147483647.0 || qtot >= 9.0e15)
+    return fail(IGASF_ERR_UNSUPPORTED, "patch too large: %.0f dofs (limit 2^31 - 1)", ntot);
   // which kernels
   ApplyKernel kern[kNumPrec];
   for (int prec = 0; prec < kNumPrec; ++prec) {
     if (!(precs & IGASF_PREC_BIT(prec))) continue;
-    if (!find_apply_kernel(d, p, prec, &kern[prec]))
+    if (!find_apply_kernel(d, p, prec, nullptr, &kern[prec]))
       return fail(IGASF_ERR_UNSUPPORTED, "no kernel for d=%d p=%d prec=%d", d, p, prec);
-    for (int a = 0; a < d; ++a)
-      if (o.tile[a] != 0 && o.tile[a] != kern[prec].S[a])
-        return fail(IGASF_ERR_UNSUPPORTED, "tile[%d] = %d is not a built shape (built: %d)", a, o.tile[a],
-                    kern[prec].S[a]);
+    if (!find_apply_kernel(d, p, prec, o.tile, &kern[prec]))
+      return fail(IGASF_ERR_UNSUPPORTED, "tile (%d, %d, %d) is not a built shape for d=%d p=%d prec=%d",
+                  o.tile[0], o.tile[1], o.tile[2], d, p, prec);
   }
   // host-side validation done: now the device
   igasf_plan *h = new (std::nothrow) igasf_plan();
@@ -280,6 +284,7 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
       v.L.T[a] = v.T[a];
     }
     v.L.plane = v.k.plane;
+    v.L.lanes = v.k.lanes;
     v.L.is_fp32 = prec == IGASF_FP32;
     const int64_t Qlast = (int64_t)v.k.S[d - 1] * p;
     const int64_t rows = (int64_t)v.ntiles * Qlast;

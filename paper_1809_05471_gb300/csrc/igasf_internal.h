@@ -37,22 +37,26 @@ struct ApplyKernel {
   int threads;                // block size
   size_t smem[2];             // dynamic shared memory, [op]
   int plane;                  // padded pencils per slab (the factor layout's row length)
+  int lanes;                  // pencils per thread (1, or 2 for packed FP32x2)
   cudaError_t (*launch[2])(const ApplyParams &, cudaStream_t);
   cudaError_t (*prepare)();   // raise the dynamic shared memory limit once
 };
 
-// Looks up the kernel for (d, p, prec); false if none is built.
-bool find_apply_kernel(int d, int p, int prec, ApplyKernel *out);
+constexpr int kMaxCandidates = 16;
 
-// Tile-major layout of the factors: for tile t, slab index s (the quadrature
-// index along the last direction inside the tile) and field f, a contiguous
-// row of `plane` entries indexed by the pencil (the lexicographic quadrature
-// index over the other directions inside the tile), zero padded.
+// The compiled kernels for (d, p, prec), default first; returns how many.
+int list_apply_kernels(int d, int p, int prec, ApplyKernel *out, int max_out);
+// The default kernel (tile all zero or NULL) or the one whose tile matches
+// every non-zero entry of `tile`; false if none is built.
+bool find_apply_kernel(int d, int p, int prec, const int *tile, ApplyKernel *out);
+
+// Tile-major layout of the factors (see layout.h for the exact order).
 struct FactorLayout {
   int d, p;
   int S[kMaxDim];
   int T[kMaxDim];
   int plane;
+  int lanes;
   int is_fp32;
   void *DM;                   // mass factors (1 field)
   void *DK;                   // stiffness factors (num_fields)

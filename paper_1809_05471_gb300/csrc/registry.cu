@@ -1,35 +1,57 @@
-// Lookup of the compiled apply kernels by (d, p, precision).
+// Lookup of the compiled apply kernels by (d, p, precision, tile shape).
 #include "igasf_internal.h"
 
 namespace igasf {
 
-ApplyKernel apply3d_p2(int prec);
-ApplyKernel apply3d_p3(int prec);
-ApplyKernel apply3d_p4(int prec);
-ApplyKernel apply3d_p5(int prec);
-ApplyKernel apply3d_p6(int prec);
-ApplyKernel apply3d_p7(int prec);
-ApplyKernel apply3d_p8(int prec);
-ApplyKernel apply3d_p9(int prec);
+int apply3d_p2(int prec, ApplyKernel *out, int max_out);
+int apply3d_p3(int prec, ApplyKernel *out, int max_out);
+int apply3d_p4(int prec, ApplyKernel *out, int max_out);
+int apply3d_p5(int prec, ApplyKernel *out, int max_out);
+int apply3d_p6(int prec, ApplyKernel *out, int max_out);
+int apply3d_p7(int prec, ApplyKernel *out, int max_out);
+int apply3d_p8(int prec, ApplyKernel *out, int max_out);
+int apply3d_p9(int prec, ApplyKernel *out, int max_out);
 ApplyKernel apply2d_any(int p, int prec);
 
-bool find_apply_kernel(int d, int p, int prec, ApplyKernel *out) {
-  if (prec != IGASF_FP64 && prec != IGASF_FP32) return false;
-  if (p < 2 || p > IGASF_MAX_ORDER) return false;
+int list_apply_kernels(int d, int p, int prec, ApplyKernel *out, int max_out) {
+  if (prec != IGASF_FP64 && prec != IGASF_FP32) return 0;
+  if (p < 2 || p > IGASF_MAX_ORDER || max_out < 1) return 0;
   if (d == 2) {
-    *out = apply2d_any(p, prec);
+    out[0] = apply2d_any(p, prec);
+    return 1;
+  }
+  if (d != 3) return 0;
+  switch (p) {
+    case 2: return apply3d_p2(prec, out, max_out);
+    case 3: return apply3d_p3(prec, out, max_out);
+    case 4: return apply3d_p4(prec, out, max_out);
+    case 5: return apply3d_p5(prec, out, max_out);
+    case 6: return apply3d_p6(prec, out, max_out);
+    case 7: return apply3d_p7(prec, out, max_out);
+    case 8: return apply3d_p8(prec, out, max_out);
+    case 9: return apply3d_p9(prec, out, max_out);
+  }
+  return 0;
+}
+
+bool find_apply_kernel(int d, int p, int prec, const int *tile, ApplyKernel *out) {
+  ApplyKernel cand[kMaxCandidates];
+  const int n = list_apply_kernels(d, p, prec, cand, kMaxCandidates);
+  if (n == 0) return false;
+  bool any = false;
+  for (int a = 0; a < d; ++a) any = any || (tile && tile[a] != 0);
+  if (!any) {
+    *out = cand[0];
     return true;
   }
-  if (d != 3) return false;
-  switch (p) {
-    case 2: *out = apply3d_p2(prec); return true;
-    case 3: *out = apply3d_p3(prec); return true;
-    case 4: *out = apply3d_p4(prec); return true;
-    case 5: *out = apply3d_p5(prec); return true;
-    case 6: *out = apply3d_p6(prec); return true;
-    case 7: *out = apply3d_p7(prec); return true;
-    case 8: *out = apply3d_p8(prec); return true;
-    case 9: *out = apply3d_p9(prec); return true;
+  for (int i = 0; i < n; ++i) {
+    bool ok = true;
+    for (int a = 0; a < d; ++a)
+      if (tile[a] != 0 && tile[a] != cand[i].S[a]) ok = false;
+    if (ok) {
+      *out = cand[i];
+      return true;
+    }
   }
   return false;
 }

@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include "igasf_internal.h"
+#include "layout.h"
 
 namespace igasf {
 
@@ -118,7 +119,8 @@ cudaError_t launch_pad_tables(int p, int K, int Qpad, const double *src, void *d
 __device__ __forceinline__ int64_t layout_index(const FactorLayout &L, int nf, int f,
                                                 const int *qg) {
   const int p = L.p;
-  int tile = 0, stride = 1, pen = 0, pstride = 1, slab = 0;
+  int64_t tile = 0, stride = 1;
+  int pen = 0, pstride = 1, slab = 0;
   for (int a = 0; a < L.d; ++a) {
     const int e = qg[a] / p;
     const int t = e / L.S[a];
@@ -132,8 +134,8 @@ __device__ __forceinline__ int64_t layout_index(const FactorLayout &L, int nf, i
       slab = ql;
     }
   }
-  const int Qlast = L.S[L.d - 1] * p;
-  return (((int64_t)tile * Qlast + slab) * nf + f) * L.plane + pen;
+  return factor_index(tile, slab, pen, f, nf, L.plane, L.S[L.d - 1] * p, L.lanes,
+                      L.is_fp32 ? 4 : 8);
 }
 
 template <typename T>
@@ -385,29 +387,51 @@ cudaError_t launch_export_factors(const FactorLayout &L, int op, int64_t Qtot, c
 // (the accumulation S_D^T v_D of eq. loc-basis-change), in a fixed tile order
 // so that the result is bitwise reproducible.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void gather_kernel(int d, const T *__restrict__ vpart, T *__restrict__ v, int N0,
-                              int N1, int N2, int T0, int T1, int T2, int S0, int S1, int S2,
-                              int p) {
-  const int64_t Ntot = (int64_t)N0 * N1 * N2;
-  const int E0 = S0 + p - 1, E1 = d > 1 ? S1 + p - 1 : 1, E2 = d > 2 ? S2 + p - 1 : 1;
-  const int64_t vol = (int64_t)E0 * E1 * E2;
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < Ntot;
-       n += (int64_t)gridDim.x * blockDim.x) {
-    const int i0 = (int)(n % N0), i1 = (int)((n / N0) % N1), i2 = (int)(n / ((int64_t)N0 * N1));
-    const int lo0 = i0 - E0 + 1 > 0 ? (i0 - E0 + S0) / S0 : 0, hi0 = min(T0 - 1, i0 / S0);
-    const int lo1 = i1 - E1 + 1 > 0 ? (i1 - E1 + S1) / S1 : 0, hi1 = min(T1 - 1, i1 / S1);
-    const int lo2 = i2 - E2 + 1 > 0 ? (i2 - E2 + S2) / S2 : 0, hi2 = min(T2 - 1, i2 / S2);
-    T acc = T(0);
+// Tiles containing index i along one direction: t*S <= i <= t*S + E - 1, 0 <= t < T.
+__device__ __forceinline__ void tile_range(int i, int S, int E, int T, int &lo, int &hi) {
+  lo = i - E + 1 > 0 ? (i - E + S) / S : 0;
+  hi = min(T - 1, i / S);
+}
+
+template <typename T, bool TWO>
+__global__ void gather_kernel(const T *__restrict__ vpart, T *__restrict__ v, int N0, int N1,
+                              int Ntot, int T0, int T1, int T2, int S0, int S1, int S2, int E0,
+                              int E1, int E2, int vol) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= Ntot) return;
+  const int i0 = n % N0, r = n / N0;
+  const int i1 = r % N1, i2 = r / N1;
+  int lo0, hi0, lo1, hi1, lo2, hi2;
+  tile_range(i0, S0, E0, T0, lo0, hi0);
+  tile_range(i1, S1, E1, T1, lo1, hi1);
+  tile_range(i2, S2, E2, T2, lo2, hi2);
+  T acc = T(0);
+  if (TWO) {
+    // at most two tiles per direction (S >= p - 1): issue all loads at once,
+    // then add in the same tile order as the general loop below
+    T x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int t2 = lo2 + (c >> 2), t1 = lo1 + ((c >> 1) & 1), t0 = lo0 + (c & 1);
+      x[c] = T(0);
+      if (t2 <= hi2 && t1 <= hi1 && t0 <= hi0) {
+        const int64_t tile = ((int64_t)t2 * T1 + t1) * T0 + t0;
+        const int loc = ((i2 - t2 * S2) * E1 + (i1 - t1 * S1)) * E0 + (i0 - t0 * S0);
+        x[c] = vpart[tile * vol + loc];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc += x[c];
+  } else {
     for (int t2 = lo2; t2 <= hi2; ++t2)
       for (int t1 = lo1; t1 <= hi1; ++t1)
         for (int t0 = lo0; t0 <= hi0; ++t0) {
           const int64_t tile = ((int64_t)t2 * T1 + t1) * T0 + t0;
-          const int64_t loc = ((int64_t)(i2 - t2 * S2) * E1 + (i1 - t1 * S1)) * E0 + (i0 - t0 * S0);
+          const int loc = ((i2 - t2 * S2) * E1 + (i1 - t1 * S1)) * E0 + (i0 - t0 * S0);
           acc += vpart[tile * vol + loc];
         }
-    v[n] = acc;
   }
+  v[n] = acc;
 }
 
 cudaError_t launch_gather(int d, int is_fp32, const void *vpart, void *v, const int *N,
@@ -415,15 +439,22 @@ cudaError_t launch_gather(int d, int is_fp32, const void *vpart, void *v, const 
   const int N1 = d > 1 ? N[1] : 1, N2 = d > 2 ? N[2] : 1;
   const int T1 = d > 1 ? T[1] : 1, T2 = d > 2 ? T[2] : 1;
   const int S1 = d > 1 ? S[1] : 1, S2 = d > 2 ? S[2] : 1;
-  const int64_t Ntot = (int64_t)N[0] * N1 * N2;
-  int blocks = (int)((Ntot + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  if (is_fp32)
-    gather_kernel<float><<<blocks, 256, 0, s>>>(d, (const float *)vpart, (float *)v, N[0], N1, N2,
-                                               T[0], T1, T2, S[0], S1, S2, p);
-  else
-    gather_kernel<double><<<blocks, 256, 0, s>>>(d, (const double *)vpart, (double *)v, N[0], N1,
-                                                N2, T[0], T1, T2, S[0], S1, S2, p);
+  const int E0 = S[0] + p - 1, E1 = d > 1 ? S1 + p - 1 : 1, E2 = d > 2 ? S2 + p - 1 : 1;
+  const int vol = E0 * E1 * E2;
+  const int Ntot = N[0] * N1 * N2;
+  const bool two = E0 <= 2 * S[0] && E1 <= 2 * S1 && E2 <= 2 * S2;
+  const int blocks = (Ntot + 255) / 256;
+#define IGASF_GATHER(TT, TWO_)                                                                 \
+  gather_kernel<TT, TWO_><<<blocks, 256, 0, s>>>((const TT *)vpart, (TT *)v, N[0], N1, Ntot, T[0], \
+                                                 T1, T2, S[0], S1, S2, E0, E1, E2, vol)
+  if (is_fp32) {
+    if (two) IGASF_GATHER(float, true);
+    else IGASF_GATHER(float, false);
+  } else {
+    if (two) IGASF_GATHER(double, true);
+    else IGASF_GATHER(double, false);
+  }
+#undef IGASF_GATHER
   return cudaGetLastError();
 }
 
