@@ -195,6 +195,28 @@ int igasf_get_factors(igasf_handle h, int op, int prec, double *out);
 int igasf_profile_begin(igasf_handle h, int max_applies);
 int igasf_profile_end(igasf_handle h, double *ms, int *applies);
 
+/*
+ * No counterpart in the paper: a deployment variant of igasf_apply_prec for
+ * callers that must not allocate device memory when they apply the operator,
+ * for instance code that hands all device memory to its own arena and forbids
+ * further cudaMalloc/cudaFree calls (both can synchronize the whole device).
+ *
+ * It computes the same v = A u with the same kernels, but its per-tile scratch
+ * (the partial results that the gather sums) lives in one static device array
+ * of IGASF_NOALLOC_SCRATCH_BYTES that the library reserves on every GPU where it
+ * is loaded, for the life of the process; it does not use the plan's own
+ * workspace and allocates nothing. Plans whose scratch need exceeds that size
+ * (igasf_describe().workspace_bytes) are rejected with IGASF_ERR_UNSUPPORTED.
+ * The first call on each device looks up the array's device address (with that
+ * device current) and must therefore come before any stream capture. All calls
+ * on a device share the array: calls whose kernels may run at the same time on
+ * the GPU race and give wrong results, so order them (one stream). The array
+ * keeps the last call's contents; nothing in it needs to start at zero.
+ * Arguments, ordering and errors are otherwise those of igasf_apply_prec.
+ */
+#define IGASF_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int igasf_apply_noalloc(igasf_handle h, int op, int prec, const void *u, void *v, void *stream);
+
 /* Message for the last error on this host thread ("" if none). */
 const char *igasf_last_error_message(void);
 

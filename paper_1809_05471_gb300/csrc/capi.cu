@@ -162,6 +162,53 @@ int alloc(void **p, size_t bytes, const char *what) {
 
 }  // namespace
 
+namespace igasf {
+
+// Used by igasf_apply_noalloc (noalloc.cu): the apply with a caller-given
+// scratch buffer in place of the plan's workspace.
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+int apply_with_workspace(igasf_plan *h, int op, int prec, const void *u, void *v, void *ws,
+                         size_t ws_bytes, void *stream) {
+  if (!h) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL");
+  if (op != IGASF_MASS && op != IGASF_STIFFNESS) return fail(IGASF_ERR_INVALID_ARG, "op = %d", op);
+  if (prec < 0 || prec >= kNumPrec) return fail(IGASF_ERR_INVALID_ARG, "prec = %d", prec);
+  Variant &var = h->var[prec];
+  if (!var.present) return fail(IGASF_ERR_UNSUPPORTED, "precision %d was not stored at setup", prec);
+  if (!u || !v) return fail(IGASF_ERR_INVALID_ARG, "u and v must be non-NULL");
+  if (var.vpart_bytes > ws_bytes)
+    return fail(IGASF_ERR_UNSUPPORTED,
+                "this plan needs %zu bytes of scratch; the static scratch holds %zu bytes",
+                var.vpart_bytes, ws_bytes);
+  const size_t es = prec_size(prec);
+  if (((uintptr_t)u % es) || ((uintptr_t)v % es))
+    return fail(IGASF_ERR_INVALID_ARG, "u and v must be aligned to %zu bytes", es);
+  const uintptr_t ub = (uintptr_t)u, vb = (uintptr_t)v, len = (uintptr_t)h->Ntot * es;
+  if (ub < vb + len && vb < ub + len) return fail(IGASF_ERR_INVALID_ARG, "u and v overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ApplyParams prm;
+  memset(&prm, 0, sizeof(prm));
+  prm.u = u;
+  prm.vpart = ws;
+  prm.D = op == IGASF_MASS ? var.L.DM : var.L.DK;
+  for (int a = 0; a < kMaxDim; ++a) {
+    prm.tabB[a] = var.tabB[a];
+    prm.tabD[a] = var.tabD[a];
+    prm.N[a] = h->N[a];
+    prm.K[a] = h->K[a];
+    prm.T[a] = var.T[a];
+    prm.Qpad[a] = var.Qpad[a];
+  }
+  prm.ntiles = var.ntiles;
+  cudaError_t e = var.k.launch[op](prm, s);
+  if (e != cudaSuccess) return cuda_fail(e, "apply kernel launch");
+  e = launch_gather(h->d, prec == IGASF_FP32, ws, v, h->N, var.T, var.k.S, h->p, s);
+  if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
+  return IGASF_OK;
+}
+
+}  // namespace igasf
+
 extern "C" {
 
 int igasf_version(void) { return IGASF_VERSION; }

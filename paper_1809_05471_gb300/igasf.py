@@ -33,7 +33,7 @@ ERRORS = {
 EXPORTED = [
     "igasf_setup", "igasf_apply", "igasf_apply_prec", "igasf_apply_host", "igasf_destroy",
     "igasf_num_dofs", "igasf_num_quad_points", "igasf_describe", "igasf_get_tables",
-    "igasf_get_factors", "igasf_profile_begin", "igasf_profile_end",
+    "igasf_get_factors", "igasf_profile_begin", "igasf_profile_end", "igasf_apply_noalloc",
     "igasf_last_error_message", "igasf_version",
 ]
 
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
     lib.igasf_describe.argtypes = [vp, ctypes.c_int, ctypes.POINTER(PlanDesc)]
     lib.igasf_get_tables.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp]
     lib.igasf_get_factors.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
+    lib.igasf_apply_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     lib.igasf_profile_begin.argtypes = [vp, ctypes.c_int]
     lib.igasf_profile_end.argtypes = [vp, dp, ip]
     lib.igasf_last_error_message.restype = ctypes.c_char_p
@@ -173,6 +174,13 @@ class Plan:
     def apply_default(self, op: int, u, v, stream=None):
         _check(load_library().igasf_apply(self._h(), int(op), u.data_ptr(), v.data_ptr(),
                                           _stream_handle(stream)))
+        return v
+
+    def apply_noalloc(self, op: int, u, v, prec: int = FP64, stream=None):
+        """v = A u with the library's static scratch instead of the plan's
+        workspace (for callers that must not allocate device memory)."""
+        _check(load_library().igasf_apply_noalloc(self._h(), int(op), int(prec), u.data_ptr(),
+                                                  v.data_ptr(), _stream_handle(stream)))
         return v
 
     def apply_host(self, op: int, u, v, prec: int = FP64, stream=None):
