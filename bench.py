@@ -91,18 +91,23 @@ def apply_flops(op, p, K, d=3):
 
 
 def traffic_record(kernel_key):
-    """DRAM bytes per launch from a committed ncu summary, if it matches the
-    current kernel source; else None."""
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current source of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_1809_05471_gb300", "csrc", "apply3d.cuh")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     ent = rec.get(kernel_key)
-    if not ent or ent.get("apply3d_cuh_sha256_16") != h:
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_1809_05471_gb300", "csrc", ent.get("source", ""))
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if ent.get("source_sha256_16") != h:
         return None
     return ent.get("dram_bytes_per_launch")
 
