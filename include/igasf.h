@@ -89,8 +89,17 @@ typedef struct {
   int default_prec;      /* precision used by igasf_apply (default IGASF_FP64) */
   int tile[3];           /* elements per tile per direction, 0 = the library's choice;
                             honoured only where a kernel is built for that shape */
-  int reserved[8];       /* must be zero */
+  int kernel_variant;    /* IGASF_KERNEL_*, 0 = the library's choice */
+  int reserved[7];       /* must be zero */
 } igasf_options;
+
+/* How the FP32 3D tile kernel receives its factors (FP64 and 2D kernels have
+ * one scheme: per-thread loads). */
+enum {
+  IGASF_KERNEL_DEFAULT = 0,
+  IGASF_KERNEL_REGISTERS = 1, /* each thread loads its factors into registers, slabs ahead */
+  IGASF_KERNEL_RING = 2       /* bulk copies into a shared-memory ring by a producer warp */
+};
 
 typedef struct igasf_plan *igasf_handle;
 
@@ -106,6 +115,7 @@ typedef struct {
                                including the zero padding of ragged tiles */
   int64_t workspace_bytes;  /* per-tile partial results of v */
   size_t smem_bytes[2];     /* dynamic shared memory per block, [op] */
+  int kernel_variant;       /* IGASF_KERNEL_* of the tile kernel */
 } igasf_plan_desc;
 
 /*
@@ -196,6 +206,25 @@ int igasf_profile_begin(igasf_handle h, int max_applies);
 int igasf_profile_end(igasf_handle h, double *ms, int *applies);
 
 /*
+ * Device status of the plan. Kernels that wait on shared-memory barriers (the
+ * FP32 3D tile kernel, whose factor stream arrives by bulk copies) bound every
+ * wait by a clock-cycle limit; a wait that runs out sets a status word on the
+ * device and the kernel finishes without hanging, but its result is invalid.
+ * This call waits for the device, then returns IGASF_ERR_TIMEOUT if the word is
+ * set (and clears it if `clear` is non-zero), IGASF_OK otherwise.
+ */
+int igasf_device_status(igasf_handle h, int clear);
+
+/*
+ * Test hook for the bounded waits: from now on, tile 0 of every FP32 3D apply
+ * on this handle never receives factor slab `skip_slab` (-1 turns this off),
+ * and every wait gives up after `wait_limit_cycles` clock cycles (default 2e9,
+ * about one second; minimum 1000). Results of applies made while a slab is
+ * skipped are invalid. Errors: INVALID_ARG.
+ */
+int igasf_set_test_fault(igasf_handle h, int skip_slab, long long wait_limit_cycles);
+
+/*
  * No counterpart in the paper: a deployment variant of igasf_apply_prec for
  * callers that must not allocate device memory when they apply the operator,
  * for instance code that hands all device memory to its own arena and forbids
@@ -216,6 +245,41 @@ int igasf_profile_end(igasf_handle h, double *ms, int *applies);
  */
 #define IGASF_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 int igasf_apply_noalloc(igasf_handle h, int op, int prec, const void *u, void *v, void *stream);
+
+/* Outcome of igasf_cg_solve. */
+typedef struct {
+  int converged;             /* 1 if ||b - K x|| <= rtol ||b|| was reached */
+  int outer_iterations;      /* FP64 residual evaluations r = b - K x */
+  int inner_iterations;      /* preconditioned CG iterations, all precisions */
+  double final_relres;       /* ||b - K x|| / ||b|| over the interior dofs, FP64 */
+  double seconds;            /* wall time of the solve, device synchronised */
+} igasf_cg_report;
+
+/*
+ * Jacobi-preconditioned conjugate gradients for K u = b with homogeneous
+ * Dirichlet conditions: the unknowns are the interior dofs (index 1..N_a - 2 in
+ * every direction; on open knot vectors only the first and last function of a
+ * direction are non-zero on the boundary), boundary dofs are held at zero. The
+ * operator is applied matrix-free (the paper's motivation for matrix-free
+ * application, Sec. 3.3 and Sec. 8: iterative solvers need only v = A u).
+ *
+ *   inner_prec = IGASF_FP64: PCG in FP64 (FP64 apply) until ||r|| <= rtol ||b||.
+ *   inner_prec = IGASF_FP32: iterative refinement. Outer loop in FP64:
+ *     r = b - K x with the FP64 apply; inner PCG on K d = r with the FP32 apply,
+ *     FP32 vectors and FP64 dot products, to ||r_inner|| <= inner_rtol ||r||;
+ *     x += d. Stops when the FP64 residual satisfies ||r|| <= rtol ||b||.
+ * The Jacobi diagonal of K is computed on the device in FP64 at the first call
+ * and kept in the plan.
+ *
+ * b, x: device arrays of num_dofs doubles (boundary entries of b are ignored);
+ * x is overwritten (the solve starts from zero). The plan must store FP64 (and
+ * FP32 for the refined solve). max_iterations bounds the total inner
+ * iterations. Synchronous; allocates its vectors for the duration of the call.
+ * report may be NULL. Errors: INVALID_ARG, UNSUPPORTED (d != 3 or a missing
+ * precision), CUDA, OOM. Not converging is not an error: see report->converged.
+ */
+int igasf_cg_solve(igasf_handle h, int inner_prec, const double *b, double *x, double rtol,
+                   double inner_rtol, int max_iterations, igasf_cg_report *report, void *stream);
 
 /* Message for the last error on this host thread ("" if none). */
 const char *igasf_last_error_message(void);

@@ -197,6 +197,7 @@ ApplyKernel make_apply2d() {
   k.smem[IGASF_STIFFNESS] = G::smem_words(true) * sizeof(T);
   k.plane = G::PL;
   k.lanes = 1;
+  k.variant = IGASF_KERNEL_REGISTERS;
   k.launch[IGASF_MASS] = &launch_apply2d<T, P, S1, S2, false>;
   k.launch[IGASF_STIFFNESS] = &launch_apply2d<T, P, S1, S2, true>;
   k.prepare = &prepare_apply2d<T, P, S1, S2>;

@@ -308,6 +308,7 @@ ApplyKernel make_apply3d() {
   k.smem[IGASF_STIFFNESS] = G::smem_words(true) * sizeof(T);
   k.plane = G::PL;
   k.lanes = 1;
+  k.variant = IGASF_KERNEL_REGISTERS;
   k.launch[IGASF_MASS] = &launch_apply3d<T, P, S1, S2, S3, false>;
   k.launch[IGASF_STIFFNESS] = &launch_apply3d<T, P, S1, S2, S3, true>;
   k.prepare = &prepare_apply3d<T, P, S1, S2, S3>;

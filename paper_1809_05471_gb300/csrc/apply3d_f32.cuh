@@ -1,5 +1,5 @@
 // FP32 tile kernel of the 3D apply with packed FP32x2 arithmetic (sm_100+
-// FFMA2): each thread owns a PAIR of neighbouring quadrature pencils
+// FFMA2): each consumer thread owns a PAIR of neighbouring quadrature pencils
 // (q1 = 2k, 2k+1 at one q2), so every per-pencil quantity is a float2 and one
 // FFMA2 advances both pencils. Same sweeps as the scalar kernel (Alg. 3, the
 // product with w F, Alg. 2, localized per Sec. 4):
@@ -12,11 +12,19 @@
 //   D  Ya = B2^T W3 + B2'^T W2, Yb = B2^T W1      (register-blocked over q2)
 //   E  v_D = B1^T Ya + B1'^T Yb                   (register-blocked over q1)
 //
-// The factors of the first PD slabs are requested at kernel entry, before
-// phases A and B, so their HBM latency overlaps the first two sweeps; in
-// phase C every slab's loads are issued PD slabs ahead of their use.
-// Tables of directions 2 and 3 are held in shared memory as duplicated pairs
-// {b, b} so that one 128-bit load feeds two FFMA2 table operands.
+// The factors stream through a ring of R slab buffers in shared memory, filled
+// by bulk copies (cp.async.bulk, the TMA engine) that one lane of a dedicated
+// producer warp issues from kernel entry on, so the factor stream overlaps the
+// staging and the first two sweeps and keeps R slabs per block in flight.
+// Each slot has a "full" mbarrier (the copy's transaction count) and an
+// "empty" mbarrier (one arrival per consumer warp once it has read the slot).
+// Every wait is bounded in clock cycles; a wait that runs out sets the plan's
+// device status word and the kernel carries on (its result is then invalid and
+// the host sees IGASF_ERR_TIMEOUT from igasf_device_status).
+// Tables of directions 2 and 3 are held as duplicated pairs {b, b} so that one
+// 128-bit load feeds two FFMA2 table operands; the X and Y arrays have padded
+// row strides so the register-blocked sweeps read shared memory without bank
+// conflicts.
 #pragma once
 
 #include "igasf_internal.h"
@@ -27,18 +35,57 @@ namespace igasf {
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-__device__ __forceinline__ float4 ldg_stream4(const float4 *p) {
-  float4 r;
-  asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-               : "l"(p));
-  return r;
+// ---- mbarrier and bulk-copy helpers (shared-memory addresses as 32-bit) ----
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ float2 ldg_stream2(const float2 *p) {
-  float2 r;
-  asm volatile("ld.global.cs.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
-  return r;
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of the given parity, at most `limit` clock cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+
+// Global -> shared bulk copy completing on an mbarrier (sizes and addresses
+// multiples of 16 bytes).
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
 template <int P, int S1, int S2, int S3>
@@ -51,30 +98,47 @@ struct TileF2 {
   static constexpr int PL = (NPEN + 31) / 32 * 32;  // plane (pencils), layout row length
   static constexpr int UNITS = PL / 2;              // pairs per layout row
   static constexpr int NPAIR = H1 * Q2;
-  static constexpr int NT = (NPAIR + 31) / 32 * 32;
+  static constexpr int NTC = (NPAIR + 31) / 32 * 32;  // consumer threads
+  static constexpr int NT = NTC + 32;                 // + one producer warp
   static constexpr int PP = P + (P & 1);            // j padded to even for 128-bit loads
+  static constexpr int XS = H1 | 1;                 // X row stride (float2), odd
+  static constexpr int YS = (NPAIR + 15) / 16 * 16 + 8;  // Y plane stride (float2)
   static constexpr int T2 = 4 * PP * Q2;            // dup tables of dir 2 (B, B'), floats
   static constexpr int T3 = 4 * PP * Q3;
   static constexpr int T1 = 2 * P * Q1;             // dir-1 tables [j][q1] (B, B')
   static constexpr int VOL = E1 * E2 * E3;
-  static constexpr int X = E3 * E2 * Q1;            // floats
-  static constexpr int Y = E3 * Q2 * Q1;            // floats
-  static constexpr size_t smem_floats(bool stiff) {
-    return (size_t)T2 + T3 + T1 + (stiff ? 2 : 1) * X + (stiff ? 3 : 1) * Y + VOL;
+  static constexpr int X = 2 * E3 * E2 * XS;        // floats per X array
+  static constexpr int Y = 2 * E3 * YS;             // floats per Y array
+  // factor slab bytes and ring depth (about 48 KB of slabs in flight per block)
+  __host__ __device__ static constexpr uint32_t slab_bytes(bool stiff) { return stiff ? 3u * UNITS * 16u : UNITS * 8u; }
+  __host__ __device__ static constexpr int ring(bool stiff) {
+    return (int)(49152u / slab_bytes(stiff)) < 2 ? 2
+           : ((int)(49152u / slab_bytes(stiff)) > Q3 ? Q3 : (int)(49152u / slab_bytes(stiff)));
+  }
+  __host__ __device__ static constexpr size_t ring_bytes(bool stiff) { return (size_t)ring(stiff) * slab_bytes(stiff); }
+  __host__ __device__ static constexpr size_t smem_bytes(bool stiff) {
+    return ring_bytes(stiff) + 16 * (size_t)ring(stiff) +
+           4 * ((size_t)T2 + T3 + T1 + (stiff ? 2 : 1) * X + (stiff ? 3 : 1) * Y + VOL);
   }
 };
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+template <int P, int S1, int S2, int S3, bool STIFF>
 __global__ void __launch_bounds__(TileF2<P, S1, S2, S3>::NT)
 apply3d_f32_kernel(const ApplyParams prm) {
   using G = TileF2<P, S1, S2, S3>;
   constexpr int E1 = G::E1, E2 = G::E2, E3 = G::E3;
   constexpr int Q1 = G::Q1, Q2 = G::Q2, Q3 = G::Q3;
-  constexpr int H1 = G::H1, PP = G::PP, NT = G::NT, NPAIR = G::NPAIR, UNITS = G::UNITS;
+  constexpr int H1 = G::H1, PP = G::PP, NTC = G::NTC, NPAIR = G::NPAIR, UNITS = G::UNITS;
+  constexpr int XS = G::XS, YS = G::YS;
+  constexpr int R = G::ring(STIFF);
+  constexpr uint32_t SB = G::slab_bytes(STIFF);
   constexpr int NCH = STIFF ? 3 : 1;   // 16-byte chunks (stiffness) or one 8-byte chunk (mass)
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float *sm = reinterpret_cast<float *>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smem_f32[];
+  unsigned char *ring = smem_f32;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_f32 + G::ring_bytes(STIFF));
+  uint64_t *empty = full + R;
+  float *sm = reinterpret_cast<float *>(empty + R);
   float *t2b = sm, *t2d = t2b + 2 * PP * Q2;        // [q2][PP] float2 {b, b}
   float *t3b = t2d + 2 * PP * Q2, *t3d = t3b + 2 * PP * Q3;
   float *t1b = t3d + 2 * PP * Q3, *t1d = t1b + P * Q1; // [j][q1]
@@ -93,22 +157,38 @@ apply3d_f32_kernel(const ApplyParams prm) {
   const int ke3 = min(S3, prm.K[2] - e03);
   const int nslab = ke3 * P;
 
-  // ---- request the first PD slabs of factors now (consumed in phase C)
-  const bool has_pair = tid < NPAIR;
-  float4 dq4[PD][NCH];
-  float2 dq2[PD];
-  const float4 *D4 = reinterpret_cast<const float4 *>(prm.D) + (size_t)tile * Q3 * NCH * UNITS + tid;
-  const float2 *D2 = reinterpret_cast<const float2 *>(prm.D) + (size_t)tile * Q3 * UNITS + tid;
-#pragma unroll
-  for (int s = 0; s < PD; ++s) {
-    if (has_pair && s < nslab) {
-      if (STIFF) {
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) dq4[s][c] = ldg_stream4(D4 + ((size_t)s * NCH + c) * UNITS);
-      } else {
-        dq2[s] = ldg_stream2(D2 + (size_t)s * UNITS);
-      }
+  if (tid == 0) {
+    for (int r = 0; r < R; ++r) {
+      mbar_init(smem_addr(&full[r]), 1);
+      mbar_init(smem_addr(&empty[r]), NTC / 32);
     }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // ---- producer warp: one lane streams the tile's factor slabs into the ring
+  if (tid >= NTC) {
+    if (tid == NTC) {
+      const unsigned char *src = static_cast<const unsigned char *>(prm.D) + (size_t)tile * Q3 * SB;
+      bool bad = false;
+      for (int s = 0; s < nslab; ++s) {
+        const int slot = s % R;
+        if (s >= R && !mbar_wait_bounded(smem_addr(&empty[slot]), ((s / R) - 1) & 1, prm.wait_limit))
+          bad = true;
+        if (tile == 0 && s == prm.skip_slab) continue;   // test hook: a fill that never comes
+        mbar_arrive_expect_tx(smem_addr(&full[slot]), SB);
+        bulk_copy_g2s(smem_addr(ring + (size_t)slot * SB), src + (size_t)s * SB, SB,
+                      smem_addr(&full[slot]));
+      }
+      // leave no copy in flight: wait for the last fill of every slot
+      const int used = nslab < R ? nslab : R;
+      for (int slot = 0; slot < used; ++slot) {
+        const int last = (nslab - 1 - slot) / R;
+        if (!mbar_wait_bounded(smem_addr(&full[slot]), last & 1, prm.wait_limit)) bad = true;
+      }
+      if (bad) atomicOr(prm.status, 1u);
+    }
+    return;
   }
 
   // ---- stage tables and the u tile (selection S_D u of eq. loc-basis-change)
@@ -116,12 +196,12 @@ apply3d_f32_kernel(const ApplyParams prm) {
     const float *gb1 = static_cast<const float *>(prm.tabB[0]), *gd1 = static_cast<const float *>(prm.tabD[0]);
     const float *gb2 = static_cast<const float *>(prm.tabB[1]), *gd2 = static_cast<const float *>(prm.tabD[1]);
     const float *gb3 = static_cast<const float *>(prm.tabB[2]), *gd3 = static_cast<const float *>(prm.tabD[2]);
-    for (int i = tid; i < P * Q1; i += NT) {
+    for (int i = tid; i < P * Q1; i += NTC) {
       const int j = i / Q1, q = i - j * Q1;
       t1b[i] = gb1[j * prm.Qpad[0] + e01 * P + q];
       if (STIFF) t1d[i] = gd1[j * prm.Qpad[0] + e01 * P + q];
     }
-    for (int i = tid; i < PP * Q2; i += NT) {
+    for (int i = tid; i < PP * Q2; i += NTC) {
       const int q = i / PP, j = i - q * PP;
       const float b = j < P ? gb2[j * prm.Qpad[1] + e02 * P + q] : 0.f;
       t2b[2 * i] = b;
@@ -132,7 +212,7 @@ apply3d_f32_kernel(const ApplyParams prm) {
         t2d[2 * i + 1] = db;
       }
     }
-    for (int i = tid; i < PP * Q3; i += NT) {
+    for (int i = tid; i < PP * Q3; i += NTC) {
       const int q = i / PP, j = i - q * PP;
       const float b = j < P ? gb3[j * prm.Qpad[2] + e03 * P + q] : 0.f;
       t3b[2 * i] = b;
@@ -145,7 +225,7 @@ apply3d_f32_kernel(const ApplyParams prm) {
     }
     const float *u = static_cast<const float *>(prm.u);
     const int N1 = prm.N[0], N2 = prm.N[1], N3 = prm.N[2];
-    for (int i = tid; i < G::VOL; i += NT) {
+    for (int i = tid; i < G::VOL; i += NTC) {
       const int n1 = i % E1, r = i / E1;
       const int n2 = r % E2, n3 = r / E2;
       const int g1 = e01 + n1, g2 = e02 + n2, g3 = e03 + n3;
@@ -154,10 +234,10 @@ apply3d_f32_kernel(const ApplyParams prm) {
       us[i] = val;
     }
   }
-  __syncthreads();
+  consumer_sync(NTC);
 
   // ---- A: direction 1, X0 = B1 u, X1 = B1' u, one pencil pair per item
-  for (int i = tid; i < E3 * E2 * H1; i += NT) {
+  for (int i = tid; i < E3 * E2 * H1; i += NTC) {
     const int k = i % H1, r = i / H1;
     const int qa = 2 * k;
     const int ea = qa / P, eb = (qa + 1) / P;
@@ -169,20 +249,20 @@ apply3d_f32_kernel(const ApplyParams prm) {
       a0 = ffma2(*reinterpret_cast<const float2 *>(t1b + j * Q1 + qa), uu, a0);
       if (STIFF) a1 = ffma2(*reinterpret_cast<const float2 *>(t1d + j * Q1 + qa), uu, a1);
     }
-    X0[i] = a0;
-    if (STIFF) X1[i] = a1;
+    X0[r * XS + k] = a0;
+    if (STIFF) X1[r * XS + k] = a1;
   }
-  __syncthreads();
+  consumer_sync(NTC);
 
   // ---- B: direction 2, one (n3, element e2, pair) per item: p inputs -> p outputs
-  for (int i = tid; i < E3 * S2 * H1; i += NT) {
+  for (int i = tid; i < E3 * S2 * H1; i += NTC) {
     const int k = i % H1, t = i / H1;
     const int e2 = t % S2, n3 = t / S2;
     float2 xa[P], xb[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      xa[j] = X0[(n3 * E2 + e2 + j) * H1 + k];
-      if (STIFF) xb[j] = X1[(n3 * E2 + e2 + j) * H1 + k];
+      xa[j] = X0[(n3 * E2 + e2 + j) * XS + k];
+      if (STIFF) xb[j] = X1[(n3 * E2 + e2 + j) * XS + k];
     }
 #pragma unroll
     for (int qq = 0; qq < P; ++qq) {
@@ -206,7 +286,7 @@ apply3d_f32_kernel(const ApplyParams prm) {
         }
         if (j1 < P) y00 = ffma2(make_float2(bb.z, bb.w), xa[j1], y00);
       }
-      const int idx = (n3 * Q2 + q2) * H1 + k;
+      const int idx = n3 * YS + q2 * H1 + k;
       Y0[idx] = y00;
       if (STIFF) {
         Y1[idx] = y01;
@@ -214,20 +294,24 @@ apply3d_f32_kernel(const ApplyParams prm) {
       }
     }
   }
-  __syncthreads();
+  consumer_sync(NTC);
 
   // ---- C: pencil pairs: direction-3 sweep, product with D, transposed sweep
-  if (has_pair) {
+  {
+    const bool has_pair = tid < NPAIR;
+    const int lane = tid & 31;
+    bool bad = false;
     float2 y0[E3], y1[E3], y2[E3], z0[E3], z1[E3], z2[E3];
 #pragma unroll
     for (int n = 0; n < E3; ++n) {
-      y0[n] = Y0[n * NPAIR + tid];
-      z0[n] = make_float2(0.f, 0.f);
+      const float2 zero = make_float2(0.f, 0.f);
+      y0[n] = has_pair ? Y0[n * YS + tid] : zero;
+      z0[n] = zero;
       if (STIFF) {
-        y1[n] = Y1[n * NPAIR + tid];
-        y2[n] = Y2[n * NPAIR + tid];
-        z1[n] = z0[n];
-        z2[n] = z0[n];
+        y1[n] = has_pair ? Y1[n * YS + tid] : zero;
+        y2[n] = has_pair ? Y2[n * YS + tid] : zero;
+        z1[n] = zero;
+        z2[n] = zero;
       }
     }
 #pragma unroll
@@ -236,24 +320,22 @@ apply3d_f32_kernel(const ApplyParams prm) {
 #pragma unroll
         for (int qq = 0; qq < P; ++qq) {
           const int q3 = e3 * P + qq;
-          // factors of this slab, then request slab q3 + PD into the freed slot
+          const int slot = q3 % R, parity = (q3 / R) & 1;   // compile-time after unrolling
+          if (!mbar_wait_bounded(smem_addr(&full[slot]), parity, prm.wait_limit)) bad = true;
           float4 dc[NCH];
           float2 dm = make_float2(0.f, 0.f);
-          if (STIFF) {
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) dc[c] = dq4[q3 % PD][c];
-          } else {
-            dm = dq2[q3 % PD];
-          }
-          if (q3 + PD < nslab) {
+          if (has_pair) {
             if (STIFF) {
+              const float4 *rs = reinterpret_cast<const float4 *>(ring + (size_t)slot * SB);
 #pragma unroll
-              for (int c = 0; c < NCH; ++c)
-                dq4[q3 % PD][c] = ldg_stream4(D4 + ((size_t)(q3 + PD) * NCH + c) * UNITS);
+              for (int c = 0; c < NCH; ++c) dc[c] = rs[c * UNITS + tid];
             } else {
-              dq2[q3 % PD] = ldg_stream2(D2 + (size_t)(q3 + PD) * UNITS);
+              dm = reinterpret_cast<const float2 *>(ring + (size_t)slot * SB)[tid];
             }
           }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_addr(&empty[slot]));
+          if (!has_pair) continue;
           float2 b[PP], db[PP];
           {
             const float4 *b4 = reinterpret_cast<const float4 *>(t3b + q3 * 2 * PP);
@@ -301,19 +383,22 @@ apply3d_f32_kernel(const ApplyParams prm) {
         }
       }
     }
+    if (has_pair) {
 #pragma unroll
-    for (int n = 0; n < E3; ++n) {
-      Y0[n * NPAIR + tid] = z0[n];
-      if (STIFF) {
-        Y1[n * NPAIR + tid] = z1[n];
-        Y2[n * NPAIR + tid] = z2[n];
+      for (int n = 0; n < E3; ++n) {
+        Y0[n * YS + tid] = z0[n];
+        if (STIFF) {
+          Y1[n * YS + tid] = z1[n];
+          Y2[n * YS + tid] = z2[n];
+        }
       }
     }
+    if (bad) atomicOr(prm.status, 1u);
   }
-  __syncthreads();
+  consumer_sync(NTC);
 
   // ---- D: transposed direction 2, register-blocked over all q2 of the tile
-  for (int i = tid; i < E3 * H1; i += NT) {
+  for (int i = tid; i < E3 * H1; i += NTC) {
     const int k = i % H1, n3 = i / H1;
     float2 ya[E2], yb[E2];
 #pragma unroll
@@ -324,7 +409,7 @@ apply3d_f32_kernel(const ApplyParams prm) {
 #pragma unroll
     for (int q2 = 0; q2 < Q2; ++q2) {
       const int e2 = q2 / P;
-      const int idx = (n3 * Q2 + q2) * H1 + k;
+      const int idx = n3 * YS + q2 * H1 + k;
       const float2 w3 = Y0[idx];
       float2 w2 = make_float2(0.f, 0.f), w1 = w2;
       if (STIFF) {
@@ -354,23 +439,23 @@ apply3d_f32_kernel(const ApplyParams prm) {
     }
 #pragma unroll
     for (int n = 0; n < E2; ++n) {
-      X0[(n3 * E2 + n) * H1 + k] = ya[n];
-      if (STIFF) X1[(n3 * E2 + n) * H1 + k] = yb[n];
+      X0[(n3 * E2 + n) * XS + k] = ya[n];
+      if (STIFF) X1[(n3 * E2 + n) * XS + k] = yb[n];
     }
   }
-  __syncthreads();
+  consumer_sync(NTC);
 
   // ---- E: transposed direction 1, one (n3, n2) row per item, all q1 in registers
   float *vp = static_cast<float *>(prm.vpart) + (size_t)tile * G::VOL;
-  for (int r = tid; r < E3 * E2; r += NT) {
+  for (int r = tid; r < E3 * E2; r += NTC) {
     float2 acc[E1];
 #pragma unroll
     for (int n = 0; n < E1; ++n) acc[n] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < H1; ++k) {
       const int qa = 2 * k, ea = qa / P, eb = (qa + 1) / P;
-      const float2 ya = X0[r * H1 + k];
-      const float2 yb = STIFF ? X1[r * H1 + k] : make_float2(0.f, 0.f);
+      const float2 ya = X0[r * XS + k];
+      const float2 yb = STIFF ? X1[r * XS + k] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < P; ++j) {
         const float2 bt = *reinterpret_cast<const float2 *>(t1b + j * Q1 + qa);
@@ -393,43 +478,43 @@ apply3d_f32_kernel(const ApplyParams prm) {
   }
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+template <int P, int S1, int S2, int S3, bool STIFF>
 cudaError_t launch_apply3d_f32(const ApplyParams &prm, cudaStream_t s) {
   using G = TileF2<P, S1, S2, S3>;
-  apply3d_f32_kernel<P, S1, S2, S3, STIFF, PD>
-      <<<prm.ntiles, G::NT, G::smem_floats(STIFF) * sizeof(float), s>>>(prm);
+  apply3d_f32_kernel<P, S1, S2, S3, STIFF><<<prm.ntiles, G::NT, G::smem_bytes(STIFF), s>>>(prm);
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, int PD>
+template <int P, int S1, int S2, int S3>
 cudaError_t prepare_apply3d_f32() {
   using G = TileF2<P, S1, S2, S3>;
-  cudaError_t e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, false, PD>,
+  cudaError_t e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(G::smem_floats(false) * sizeof(float)));
+                                       (int)G::smem_bytes(false));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, true, PD>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(G::smem_floats(true) * sizeof(float)));
+  return cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes(true));
 }
 
-template <int P, int S1, int S2, int S3, int PD = 2>
+template <int P, int S1, int S2, int S3>
 ApplyKernel make_apply3d_f32() {
   using G = TileF2<P, S1, S2, S3>;
   static_assert(G::NT <= 1024, "tile too large for one block");
-  static_assert(G::smem_floats(true) * sizeof(float) <= 227 * 1024, "tile exceeds shared memory");
+  static_assert(G::smem_bytes(true) <= 227 * 1024, "tile exceeds shared memory");
+  static_assert(G::slab_bytes(false) % 16 == 0, "bulk copies move multiples of 16 bytes");
   ApplyKernel k;
   k.S[0] = S1;
   k.S[1] = S2;
   k.S[2] = S3;
   k.threads = G::NT;
-  k.smem[IGASF_MASS] = G::smem_floats(false) * sizeof(float);
-  k.smem[IGASF_STIFFNESS] = G::smem_floats(true) * sizeof(float);
+  k.smem[IGASF_MASS] = G::smem_bytes(false);
+  k.smem[IGASF_STIFFNESS] = G::smem_bytes(true);
   k.plane = G::PL;
   k.lanes = 2;
-  k.launch[IGASF_MASS] = &launch_apply3d_f32<P, S1, S2, S3, false, PD>;
-  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32<P, S1, S2, S3, true, PD>;
-  k.prepare = &prepare_apply3d_f32<P, S1, S2, S3, PD>;
+  k.variant = IGASF_KERNEL_RING;
+  k.launch[IGASF_MASS] = &launch_apply3d_f32<P, S1, S2, S3, false>;
+  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32<P, S1, S2, S3, true>;
+  k.prepare = &prepare_apply3d_f32<P, S1, S2, S3>;
   return k;
 }
 

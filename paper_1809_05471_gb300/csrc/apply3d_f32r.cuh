@@ -1,0 +1,442 @@
+// FP32 tile kernel, register-prefetch variant: the same packed FP32x2 sweeps as
+// apply3d_f32.cuh, but each thread loads its own factors straight from HBM into
+// registers, PD slabs ahead (the first PD slabs at kernel entry). No producer
+// warp and no shared-memory ring: fewer instructions and no barrier waits,
+// fewer bytes in flight. Which variant is faster depends on the order and the
+// tile (both are tile-search candidates).
+//
+// Each thread owns a PAIR of neighbouring quadrature pencils
+// (q1 = 2k, 2k+1 at one q2), so every per-pencil quantity is a float2 and one
+// FFMA2 advances both pencils. Same sweeps as the scalar kernel (Alg. 3, the
+// product with w F, Alg. 2, localized per Sec. 4):
+//
+//   A  X0 = B1 u, X1 = B1' u                      [n3][n2][k]  float2, shared
+//   B  Y00 = B2 X0, Y01 = B2' X0, Y10 = B2 X1     [n3][q2][k]  float2, shared
+//      (each item holds the p dofs of one element in registers, emits its p q2)
+//   C  per pencil pair, in registers: d3 u = B3' Y00, d2 u = B3 Y01,
+//      d1 u = B3 Y10; g = D grad u; W3 = B3'^T g3, W2 = B3^T g2, W1 = B3^T g1
+//   D  Ya = B2^T W3 + B2'^T W2, Yb = B2^T W1      (register-blocked over q2)
+//   E  v_D = B1^T Ya + B1'^T Yb                   (register-blocked over q1)
+//
+// The factors of the first PD slabs are requested at kernel entry, before
+// phases A and B, so their HBM latency overlaps the first two sweeps; in
+// phase C every slab's loads are issued PD slabs ahead of their use.
+// Tables of directions 2 and 3 are held in shared memory as duplicated pairs
+// {b, b} so that one 128-bit load feeds two FFMA2 table operands.
+#pragma once
+
+#include "apply3d_f32.cuh"
+#include "igasf_internal.h"
+#include "layout.h"
+
+namespace igasf {
+
+
+__device__ __forceinline__ float4 ldg_stream4(const float4 *p) {
+  float4 r;
+  asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "l"(p));
+  return r;
+}
+
+__device__ __forceinline__ float2 ldg_stream2(const float2 *p) {
+  float2 r;
+  asm volatile("ld.global.cs.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
+  return r;
+}
+
+template <int P, int S1, int S2, int S3>
+struct TileF2R {
+  static constexpr int E1 = S1 + P - 1, E2 = S2 + P - 1, E3 = S3 + P - 1;
+  static constexpr int Q1 = S1 * P, Q2 = S2 * P, Q3 = S3 * P;
+  static_assert(Q1 % 2 == 0, "pencil pairs need an even number of q1 points per tile");
+  static constexpr int H1 = Q1 / 2;                 // pencil pairs per q1 row
+  static constexpr int NPEN = Q1 * Q2;
+  static constexpr int PL = (NPEN + 31) / 32 * 32;  // plane (pencils), layout row length
+  static constexpr int UNITS = PL / 2;              // pairs per layout row
+  static constexpr int NPAIR = H1 * Q2;
+  static constexpr int NT = (NPAIR + 31) / 32 * 32;
+  static constexpr int PP = P + (P & 1);            // j padded to even for 128-bit loads
+  static constexpr int T2 = 4 * PP * Q2;            // dup tables of dir 2 (B, B'), floats
+  static constexpr int T3 = 4 * PP * Q3;
+  static constexpr int T1 = 2 * P * Q1;             // dir-1 tables [j][q1] (B, B')
+  static constexpr int VOL = E1 * E2 * E3;
+  static constexpr int X = E3 * E2 * Q1;            // floats
+  static constexpr int Y = E3 * Q2 * Q1;            // floats
+  static constexpr size_t smem_floats(bool stiff) {
+    return (size_t)T2 + T3 + T1 + (stiff ? 2 : 1) * X + (stiff ? 3 : 1) * Y + VOL;
+  }
+};
+
+template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+__global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
+apply3d_f32r_kernel(const ApplyParams prm) {
+  using G = TileF2R<P, S1, S2, S3>;
+  constexpr int E1 = G::E1, E2 = G::E2, E3 = G::E3;
+  constexpr int Q1 = G::Q1, Q2 = G::Q2, Q3 = G::Q3;
+  constexpr int H1 = G::H1, PP = G::PP, NT = G::NT, NPAIR = G::NPAIR, UNITS = G::UNITS;
+  constexpr int NCH = STIFF ? 3 : 1;   // 16-byte chunks (stiffness) or one 8-byte chunk (mass)
+
+  extern __shared__ __align__(16) unsigned char smem_f32r[];
+  float *sm = reinterpret_cast<float *>(smem_f32r);
+  float *t2b = sm, *t2d = t2b + 2 * PP * Q2;        // [q2][PP] float2 {b, b}
+  float *t3b = t2d + 2 * PP * Q2, *t3d = t3b + 2 * PP * Q3;
+  float *t1b = t3d + 2 * PP * Q3, *t1d = t1b + P * Q1; // [j][q1]
+  float2 *X0 = reinterpret_cast<float2 *>(t1d + P * Q1);
+  float2 *X1 = X0 + G::X / 2;
+  float2 *Y0 = STIFF ? X1 + G::X / 2 : X0 + G::X / 2;
+  float2 *Y1 = Y0 + G::Y / 2, *Y2 = Y1 + G::Y / 2;
+  float *us = reinterpret_cast<float *>(STIFF ? Y2 + G::Y / 2 : Y0 + G::Y / 2);
+
+  const int tid = threadIdx.x;
+  const int tile = blockIdx.x;
+  const int t1 = tile % prm.T[0];
+  const int t2 = (tile / prm.T[0]) % prm.T[1];
+  const int t3 = tile / (prm.T[0] * prm.T[1]);
+  const int e01 = t1 * S1, e02 = t2 * S2, e03 = t3 * S3;
+  const int ke3 = min(S3, prm.K[2] - e03);
+  const int nslab = ke3 * P;
+
+  // ---- request the first PD slabs of factors now (consumed in phase C)
+  const bool has_pair = tid < NPAIR;
+  float4 dq4[PD][NCH];
+  float2 dq2[PD];
+  const float4 *D4 = reinterpret_cast<const float4 *>(prm.D) + (size_t)tile * Q3 * NCH * UNITS + tid;
+  const float2 *D2 = reinterpret_cast<const float2 *>(prm.D) + (size_t)tile * Q3 * UNITS + tid;
+#pragma unroll
+  for (int s = 0; s < PD; ++s) {
+    if (has_pair && s < nslab) {
+      if (STIFF) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) dq4[s][c] = ldg_stream4(D4 + ((size_t)s * NCH + c) * UNITS);
+      } else {
+        dq2[s] = ldg_stream2(D2 + (size_t)s * UNITS);
+      }
+    }
+  }
+
+  // ---- stage tables and the u tile (selection S_D u of eq. loc-basis-change)
+  {
+    const float *gb1 = static_cast<const float *>(prm.tabB[0]), *gd1 = static_cast<const float *>(prm.tabD[0]);
+    const float *gb2 = static_cast<const float *>(prm.tabB[1]), *gd2 = static_cast<const float *>(prm.tabD[1]);
+    const float *gb3 = static_cast<const float *>(prm.tabB[2]), *gd3 = static_cast<const float *>(prm.tabD[2]);
+    for (int i = tid; i < P * Q1; i += NT) {
+      const int j = i / Q1, q = i - j * Q1;
+      t1b[i] = gb1[j * prm.Qpad[0] + e01 * P + q];
+      if (STIFF) t1d[i] = gd1[j * prm.Qpad[0] + e01 * P + q];
+    }
+    for (int i = tid; i < PP * Q2; i += NT) {
+      const int q = i / PP, j = i - q * PP;
+      const float b = j < P ? gb2[j * prm.Qpad[1] + e02 * P + q] : 0.f;
+      t2b[2 * i] = b;
+      t2b[2 * i + 1] = b;
+      if (STIFF) {
+        const float db = j < P ? gd2[j * prm.Qpad[1] + e02 * P + q] : 0.f;
+        t2d[2 * i] = db;
+        t2d[2 * i + 1] = db;
+      }
+    }
+    for (int i = tid; i < PP * Q3; i += NT) {
+      const int q = i / PP, j = i - q * PP;
+      const float b = j < P ? gb3[j * prm.Qpad[2] + e03 * P + q] : 0.f;
+      t3b[2 * i] = b;
+      t3b[2 * i + 1] = b;
+      if (STIFF) {
+        const float db = j < P ? gd3[j * prm.Qpad[2] + e03 * P + q] : 0.f;
+        t3d[2 * i] = db;
+        t3d[2 * i + 1] = db;
+      }
+    }
+    const float *u = static_cast<const float *>(prm.u);
+    const int N1 = prm.N[0], N2 = prm.N[1], N3 = prm.N[2];
+    for (int i = tid; i < G::VOL; i += NT) {
+      const int n1 = i % E1, r = i / E1;
+      const int n2 = r % E2, n3 = r / E2;
+      const int g1 = e01 + n1, g2 = e02 + n2, g3 = e03 + n3;
+      float val = 0.f;
+      if (g1 < N1 && g2 < N2 && g3 < N3) val = u[((int64_t)g3 * N2 + g2) * N1 + g1];
+      us[i] = val;
+    }
+  }
+  __syncthreads();
+
+  // ---- A: direction 1, X0 = B1 u, X1 = B1' u, one pencil pair per item
+  for (int i = tid; i < E3 * E2 * H1; i += NT) {
+    const int k = i % H1, r = i / H1;
+    const int qa = 2 * k;
+    const int ea = qa / P, eb = (qa + 1) / P;
+    const float *ur = us + r * E1;
+    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const float2 uu = make_float2(ur[ea + j], ur[eb + j]);
+      a0 = ffma2(*reinterpret_cast<const float2 *>(t1b + j * Q1 + qa), uu, a0);
+      if (STIFF) a1 = ffma2(*reinterpret_cast<const float2 *>(t1d + j * Q1 + qa), uu, a1);
+    }
+    X0[i] = a0;
+    if (STIFF) X1[i] = a1;
+  }
+  __syncthreads();
+
+  // ---- B: direction 2, one (n3, element e2, pair) per item: p inputs -> p outputs
+  for (int i = tid; i < E3 * S2 * H1; i += NT) {
+    const int k = i % H1, t = i / H1;
+    const int e2 = t % S2, n3 = t / S2;
+    float2 xa[P], xb[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      xa[j] = X0[(n3 * E2 + e2 + j) * H1 + k];
+      if (STIFF) xb[j] = X1[(n3 * E2 + e2 + j) * H1 + k];
+    }
+#pragma unroll
+    for (int qq = 0; qq < P; ++qq) {
+      const int q2 = e2 * P + qq;
+      const float4 *b4 = reinterpret_cast<const float4 *>(t2b + q2 * 2 * PP);
+      const float4 *d4 = reinterpret_cast<const float4 *>(t2d + q2 * 2 * PP);
+      float2 y00 = make_float2(0.f, 0.f), y01 = y00, y10 = y00;
+#pragma unroll
+      for (int jj = 0; jj < PP / 2; ++jj) {
+        const float4 bb = b4[jj];
+        const int j0 = 2 * jj, j1 = 2 * jj + 1;
+        y00 = ffma2(make_float2(bb.x, bb.y), xa[j0], y00);
+        if (STIFF) {
+          const float4 dd = d4[jj];
+          y01 = ffma2(make_float2(dd.x, dd.y), xa[j0], y01);
+          y10 = ffma2(make_float2(bb.x, bb.y), xb[j0], y10);
+          if (j1 < P) {
+            y01 = ffma2(make_float2(dd.z, dd.w), xa[j1], y01);
+            y10 = ffma2(make_float2(bb.z, bb.w), xb[j1], y10);
+          }
+        }
+        if (j1 < P) y00 = ffma2(make_float2(bb.z, bb.w), xa[j1], y00);
+      }
+      const int idx = (n3 * Q2 + q2) * H1 + k;
+      Y0[idx] = y00;
+      if (STIFF) {
+        Y1[idx] = y01;
+        Y2[idx] = y10;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- C: pencil pairs: direction-3 sweep, product with D, transposed sweep
+  if (has_pair) {
+    float2 y0[E3], y1[E3], y2[E3], z0[E3], z1[E3], z2[E3];
+#pragma unroll
+    for (int n = 0; n < E3; ++n) {
+      y0[n] = Y0[n * NPAIR + tid];
+      z0[n] = make_float2(0.f, 0.f);
+      if (STIFF) {
+        y1[n] = Y1[n * NPAIR + tid];
+        y2[n] = Y2[n * NPAIR + tid];
+        z1[n] = z0[n];
+        z2[n] = z0[n];
+      }
+    }
+#pragma unroll
+    for (int e3 = 0; e3 < S3; ++e3) {
+      if (e3 < ke3) {
+#pragma unroll
+        for (int qq = 0; qq < P; ++qq) {
+          const int q3 = e3 * P + qq;
+          // factors of this slab, then request slab q3 + PD into the freed slot
+          float4 dc[NCH];
+          float2 dm = make_float2(0.f, 0.f);
+          if (STIFF) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) dc[c] = dq4[q3 % PD][c];
+          } else {
+            dm = dq2[q3 % PD];
+          }
+          if (q3 + PD < nslab) {
+            if (STIFF) {
+#pragma unroll
+              for (int c = 0; c < NCH; ++c)
+                dq4[q3 % PD][c] = ldg_stream4(D4 + ((size_t)(q3 + PD) * NCH + c) * UNITS);
+            } else {
+              dq2[q3 % PD] = ldg_stream2(D2 + (size_t)(q3 + PD) * UNITS);
+            }
+          }
+          float2 b[PP], db[PP];
+          {
+            const float4 *b4 = reinterpret_cast<const float4 *>(t3b + q3 * 2 * PP);
+            const float4 *d4 = reinterpret_cast<const float4 *>(t3d + q3 * 2 * PP);
+#pragma unroll
+            for (int jj = 0; jj < PP / 2; ++jj) {
+              const float4 bb = b4[jj];
+              b[2 * jj] = make_float2(bb.x, bb.y);
+              b[2 * jj + 1] = make_float2(bb.z, bb.w);
+              if (STIFF) {
+                const float4 dd = d4[jj];
+                db[2 * jj] = make_float2(dd.x, dd.y);
+                db[2 * jj + 1] = make_float2(dd.z, dd.w);
+              }
+            }
+          }
+          if (STIFF) {
+            float2 d1 = make_float2(0.f, 0.f), d2 = d1, d3 = d1;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              d3 = ffma2(db[j], y0[e3 + j], d3);
+              d2 = ffma2(b[j], y1[e3 + j], d2);
+              d1 = ffma2(b[j], y2[e3 + j], d1);
+            }
+            const float2 D11 = make_float2(dc[0].x, dc[0].y), D12 = make_float2(dc[0].z, dc[0].w);
+            const float2 D13 = make_float2(dc[1].x, dc[1].y), D22 = make_float2(dc[1].z, dc[1].w);
+            const float2 D23 = make_float2(dc[2].x, dc[2].y), D33 = make_float2(dc[2].z, dc[2].w);
+            const float2 g1 = ffma2(D13, d3, ffma2(D12, d2, fmul2(D11, d1)));
+            const float2 g2 = ffma2(D23, d3, ffma2(D22, d2, fmul2(D12, d1)));
+            const float2 g3 = ffma2(D33, d3, ffma2(D23, d2, fmul2(D13, d1)));
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              z0[e3 + j] = ffma2(db[j], g3, z0[e3 + j]);   // W3
+              z1[e3 + j] = ffma2(b[j], g2, z1[e3 + j]);    // W2
+              z2[e3 + j] = ffma2(b[j], g1, z2[e3 + j]);    // W1
+            }
+          } else {
+            float2 uq = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < P; ++j) uq = ffma2(b[j], y0[e3 + j], uq);
+            const float2 w = fmul2(dm, uq);
+#pragma unroll
+            for (int j = 0; j < P; ++j) z0[e3 + j] = ffma2(b[j], w, z0[e3 + j]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < E3; ++n) {
+      Y0[n * NPAIR + tid] = z0[n];
+      if (STIFF) {
+        Y1[n * NPAIR + tid] = z1[n];
+        Y2[n * NPAIR + tid] = z2[n];
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- D: transposed direction 2, register-blocked over all q2 of the tile
+  for (int i = tid; i < E3 * H1; i += NT) {
+    const int k = i % H1, n3 = i / H1;
+    float2 ya[E2], yb[E2];
+#pragma unroll
+    for (int n = 0; n < E2; ++n) {
+      ya[n] = make_float2(0.f, 0.f);
+      yb[n] = ya[n];
+    }
+#pragma unroll
+    for (int q2 = 0; q2 < Q2; ++q2) {
+      const int e2 = q2 / P;
+      const int idx = (n3 * Q2 + q2) * H1 + k;
+      const float2 w3 = Y0[idx];
+      float2 w2 = make_float2(0.f, 0.f), w1 = w2;
+      if (STIFF) {
+        w2 = Y1[idx];
+        w1 = Y2[idx];
+      }
+      const float4 *b4 = reinterpret_cast<const float4 *>(t2b + q2 * 2 * PP);
+      const float4 *d4 = reinterpret_cast<const float4 *>(t2d + q2 * 2 * PP);
+#pragma unroll
+      for (int jj = 0; jj < PP / 2; ++jj) {
+        const float4 bb = b4[jj];
+        const float4 dd = STIFF ? d4[jj] : bb;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = 2 * jj + h;
+          if (j < P) {
+            const float2 bj = h ? make_float2(bb.z, bb.w) : make_float2(bb.x, bb.y);
+            ya[e2 + j] = ffma2(bj, w3, ya[e2 + j]);
+            if (STIFF) {
+              const float2 dj = h ? make_float2(dd.z, dd.w) : make_float2(dd.x, dd.y);
+              ya[e2 + j] = ffma2(dj, w2, ya[e2 + j]);
+              yb[e2 + j] = ffma2(bj, w1, yb[e2 + j]);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < E2; ++n) {
+      X0[(n3 * E2 + n) * H1 + k] = ya[n];
+      if (STIFF) X1[(n3 * E2 + n) * H1 + k] = yb[n];
+    }
+  }
+  __syncthreads();
+
+  // ---- E: transposed direction 1, one (n3, n2) row per item, all q1 in registers
+  float *vp = static_cast<float *>(prm.vpart) + (size_t)tile * G::VOL;
+  for (int r = tid; r < E3 * E2; r += NT) {
+    float2 acc[E1];
+#pragma unroll
+    for (int n = 0; n < E1; ++n) acc[n] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < H1; ++k) {
+      const int qa = 2 * k, ea = qa / P, eb = (qa + 1) / P;
+      const float2 ya = X0[r * H1 + k];
+      const float2 yb = STIFF ? X1[r * H1 + k] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const float2 bt = *reinterpret_cast<const float2 *>(t1b + j * Q1 + qa);
+        const float2 dt = STIFF ? *reinterpret_cast<const float2 *>(t1d + j * Q1 + qa) : bt;
+        if (ea == eb) {
+          acc[ea + j] = ffma2(bt, ya, acc[ea + j]);
+          if (STIFF) acc[ea + j] = ffma2(dt, yb, acc[ea + j]);
+        } else {
+          acc[ea + j].x = fmaf(bt.x, ya.x, acc[ea + j].x);
+          acc[eb + j].y = fmaf(bt.y, ya.y, acc[eb + j].y);
+          if (STIFF) {
+            acc[ea + j].x = fmaf(dt.x, yb.x, acc[ea + j].x);
+            acc[eb + j].y = fmaf(dt.y, yb.y, acc[eb + j].y);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < E1; ++n) vp[r * E1 + n] = acc[n].x + acc[n].y;
+  }
+}
+
+template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+cudaError_t launch_apply3d_f32r(const ApplyParams &prm, cudaStream_t s) {
+  using G = TileF2R<P, S1, S2, S3>;
+  apply3d_f32r_kernel<P, S1, S2, S3, STIFF, PD>
+      <<<prm.ntiles, G::NT, G::smem_floats(STIFF) * sizeof(float), s>>>(prm);
+  return cudaGetLastError();
+}
+
+template <int P, int S1, int S2, int S3, int PD>
+cudaError_t prepare_apply3d_f32r() {
+  using G = TileF2R<P, S1, S2, S3>;
+  cudaError_t e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, false, PD>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(G::smem_floats(false) * sizeof(float)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, true, PD>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(G::smem_floats(true) * sizeof(float)));
+}
+
+template <int P, int S1, int S2, int S3, int PD = 2>
+ApplyKernel make_apply3d_f32r() {
+  using G = TileF2R<P, S1, S2, S3>;
+  static_assert(G::NT <= 1024, "tile too large for one block");
+  static_assert(G::smem_floats(true) * sizeof(float) <= 227 * 1024, "tile exceeds shared memory");
+  ApplyKernel k;
+  k.S[0] = S1;
+  k.S[1] = S2;
+  k.S[2] = S3;
+  k.threads = G::NT;
+  k.smem[IGASF_MASS] = G::smem_floats(false) * sizeof(float);
+  k.smem[IGASF_STIFFNESS] = G::smem_floats(true) * sizeof(float);
+  k.plane = G::PL;
+  k.lanes = 2;
+  k.variant = IGASF_KERNEL_REGISTERS;
+  k.launch[IGASF_MASS] = &launch_apply3d_f32r<P, S1, S2, S3, false, PD>;
+  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32r<P, S1, S2, S3, true, PD>;
+  k.prepare = &prepare_apply3d_f32r<P, S1, S2, S3, PD>;
+  return k;
+}
+
+}  // namespace igasf

@@ -11,6 +11,7 @@
 
 #include "igasf.h"
 #include "igasf_internal.h"
+#include "plan.h"
 
 using namespace igasf;
 
@@ -34,41 +35,6 @@ int cuda_fail(cudaError_t e, const char *what) {
   return fail(IGASF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-struct Variant {
-  bool present = false;
-  ApplyKernel k{};
-  FactorLayout L{};
-  void *tabB[kMaxDim] = {nullptr, nullptr, nullptr};
-  void *tabD[kMaxDim] = {nullptr, nullptr, nullptr};
-  int T[kMaxDim] = {1, 1, 1};
-  int Qpad[kMaxDim] = {0, 0, 0};
-  int ntiles = 0;
-  size_t bytesM = 0, bytesK = 0;
-  void *vpart = nullptr;
-  size_t vpart_bytes = 0;
-  void *u_stage = nullptr, *v_stage = nullptr;
-};
-
-}  // namespace
-
-struct igasf_plan {
-  int d = 0, p = 0, device = 0;
-  int N[kMaxDim] = {1, 1, 1}, K[kMaxDim] = {1, 1, 1}, Q[kMaxDim] = {1, 1, 1};
-  int64_t Ntot = 0, Qtot = 0;
-  double *knots[kMaxDim] = {nullptr, nullptr, nullptr};
-  int *span[kMaxDim] = {nullptr, nullptr, nullptr};
-  double *nodes[kMaxDim] = {nullptr, nullptr, nullptr};
-  double *weights[kMaxDim] = {nullptr, nullptr, nullptr};
-  double *tabB[kMaxDim] = {nullptr, nullptr, nullptr};  // FP64 [j][Q]
-  double *tabD[kMaxDim] = {nullptr, nullptr, nullptr};
-  int default_prec = IGASF_FP64;
-  Variant var[kNumPrec];
-  std::vector<cudaEvent_t> prof_events;  // 3 per timed apply
-  int prof_next = 0;                     // applies recorded so far
-};
-
-namespace {
-
 void destroy_events(igasf_plan *h) {
   for (cudaEvent_t e : h->prof_events) cudaEventDestroy(e);
   h->prof_events.clear();
@@ -78,6 +44,9 @@ void destroy_events(igasf_plan *h) {
 void free_plan(igasf_plan *h) {
   if (!h) return;
   destroy_events(h);
+  cudaFree(h->status);
+  cudaFree(h->dinv64);
+  cudaFree(h->dinv32);
   for (int a = 0; a < kMaxDim; ++a) {
     cudaFree(h->knots[a]);
     cudaFree(h->span[a]);
@@ -200,6 +169,9 @@ int apply_with_workspace(igasf_plan *h, int op, int prec, const void *u, void *v
     prm.Qpad[a] = var.Qpad[a];
   }
   prm.ntiles = var.ntiles;
+  prm.status = h->status;
+  prm.wait_limit = h->wait_limit;
+  prm.skip_slab = h->skip_slab;
   cudaError_t e = var.k.launch[op](prm, s);
   if (e != cudaSuccess) return cuda_fail(e, "apply kernel launch");
   e = launch_gather(h->d, prec == IGASF_FP32, ws, v, h->N, var.T, var.k.S, h->p, s);
@@ -235,6 +207,8 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
   if (opt) o = *opt;
   for (int r : o.reserved)
     if (r != 0) return fail(IGASF_ERR_INVALID_ARG, "options.reserved must be zero");
+  if (o.kernel_variant < 0 || o.kernel_variant > IGASF_KERNEL_RING)
+    return fail(IGASF_ERR_INVALID_ARG, "options.kernel_variant = %d", o.kernel_variant);
   if (o.default_prec != IGASF_FP64 && o.default_prec != IGASF_FP32)
     return fail(IGASF_ERR_INVALID_ARG, "options.default_prec = %d", o.default_prec);
   unsigned precs = o.precisions ? o.precisions : IGASF_PREC_BIT(o.default_prec);
@@ -266,11 +240,12 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
   ApplyKernel kern[kNumPrec];
   for (int prec = 0; prec < kNumPrec; ++prec) {
     if (!(precs & IGASF_PREC_BIT(prec))) continue;
-    if (!find_apply_kernel(d, p, prec, nullptr, &kern[prec]))
+    if (!find_apply_kernel(d, p, prec, nullptr, 0, &kern[prec]))
       return fail(IGASF_ERR_UNSUPPORTED, "no kernel for d=%d p=%d prec=%d", d, p, prec);
-    if (!find_apply_kernel(d, p, prec, o.tile, &kern[prec]))
-      return fail(IGASF_ERR_UNSUPPORTED, "tile (%d, %d, %d) is not a built shape for d=%d p=%d prec=%d",
-                  o.tile[0], o.tile[1], o.tile[2], d, p, prec);
+    if (!find_apply_kernel(d, p, prec, o.tile, o.kernel_variant, &kern[prec]))
+      return fail(IGASF_ERR_UNSUPPORTED,
+                  "tile (%d, %d, %d) with kernel variant %d is not built for d=%d p=%d prec=%d",
+                  o.tile[0], o.tile[1], o.tile[2], o.kernel_variant, d, p, prec);
   }
   // host-side validation done: now the device
   igasf_plan *h = new (std::nothrow) igasf_plan();
@@ -279,6 +254,8 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
   h->p = p;
   h->default_prec = o.default_prec;
   TRY_CUDA(cudaGetDevice(&h->device), "cudaGetDevice");
+  TRY(alloc((void **)&h->status, sizeof(unsigned int), "status word"));
+  TRY_CUDA(cudaMemset(h->status, 0, sizeof(unsigned int)), "status word");
   h->Ntot = 1;
   h->Qtot = 1;
   for (int a = 0; a < d; ++a) {
@@ -436,6 +413,9 @@ int igasf_apply_prec(igasf_handle h, int op, int prec, const void *u, void *v, v
     prm.Qpad[a] = var.Qpad[a];
   }
   prm.ntiles = var.ntiles;
+  prm.status = h->status;
+  prm.wait_limit = h->wait_limit;
+  prm.skip_slab = h->skip_slab;
   cudaEvent_t *ev = nullptr;
   if ((size_t)(h->prof_next + 1) * 3 <= h->prof_events.size()) {
     ev = &h->prof_events[(size_t)h->prof_next * 3];
@@ -528,6 +508,25 @@ int igasf_profile_end(igasf_handle h, double *ms, int *applies) {
   return IGASF_OK;
 }
 
+int igasf_device_status(igasf_handle h, int clear) {
+  if (!h) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL");
+  unsigned int st = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear && st) e = cudaMemset(h->status, 0, sizeof(st));
+  if (e != cudaSuccess) return cuda_fail(e, "read the device status word");
+  if (st) return fail(IGASF_ERR_TIMEOUT, "a bounded device wait ran out: results since the last clear are invalid");
+  return IGASF_OK;
+}
+
+int igasf_set_test_fault(igasf_handle h, int skip_slab, long long wait_limit_cycles) {
+  if (!h) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL");
+  if (wait_limit_cycles < 1000) return fail(IGASF_ERR_INVALID_ARG, "wait limit below 1000 cycles");
+  h->skip_slab = skip_slab;
+  h->wait_limit = wait_limit_cycles;
+  return IGASF_OK;
+}
+
 int64_t igasf_num_dofs(igasf_handle h) { return h ? h->Ntot : -1; }
 
 int64_t igasf_num_quad_points(igasf_handle h) { return h ? h->Qtot : -1; }
@@ -545,6 +544,7 @@ int igasf_describe(igasf_handle h, int prec, igasf_plan_desc *out) {
     out->tiles[a] = v.T[a];
   }
   out->threads_per_block = v.k.threads;
+  out->kernel_variant = v.k.variant;
   out->num_dofs = h->Ntot;
   out->num_quad_points = h->Qtot;
   out->factor_bytes[IGASF_MASS] = (int64_t)v.bytesM;

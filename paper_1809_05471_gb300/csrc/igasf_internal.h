@@ -29,6 +29,9 @@ struct ApplyParams {
   int T[kMaxDim];             // tiles per direction
   int Qpad[kMaxDim];          // T * S * p: row stride of the tables
   int ntiles;
+  unsigned int *status;       // device word: bit 0 set when a bounded wait ran out
+  long long wait_limit;       // clock cycles a kernel may wait on one mbarrier phase
+  int skip_slab;              // test hook: tile 0 never fills this factor slab (-1: off)
 };
 
 // A compiled apply kernel for one (d, p, precision) and its tile shape.
@@ -38,17 +41,19 @@ struct ApplyKernel {
   size_t smem[2];             // dynamic shared memory, [op]
   int plane;                  // padded pencils per slab (the factor layout's row length)
   int lanes;                  // pencils per thread (1, or 2 for packed FP32x2)
+  int variant;                // IGASF_KERNEL_* (which factor-stream scheme)
   cudaError_t (*launch[2])(const ApplyParams &, cudaStream_t);
   cudaError_t (*prepare)();   // raise the dynamic shared memory limit once
 };
 
-constexpr int kMaxCandidates = 16;
+constexpr int kMaxCandidates = 16;  // compiled shapes per (d, p, precision)
 
 // The compiled kernels for (d, p, prec), default first; returns how many.
 int list_apply_kernels(int d, int p, int prec, ApplyKernel *out, int max_out);
-// The default kernel (tile all zero or NULL) or the one whose tile matches
-// every non-zero entry of `tile`; false if none is built.
-bool find_apply_kernel(int d, int p, int prec, const int *tile, ApplyKernel *out);
+// The default kernel (tile all zero or NULL, variant 0) or the first one whose
+// tile matches every non-zero entry of `tile` and whose variant matches a
+// non-zero `variant`; false if none is built.
+bool find_apply_kernel(int d, int p, int prec, const int *tile, int variant, ApplyKernel *out);
 
 // Tile-major layout of the factors (see layout.h for the exact order).
 struct FactorLayout {

@@ -1,0 +1,49 @@
+// The plan behind an igasf_handle (shared by the C-ABI translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "igasf_internal.h"
+
+namespace igasf {
+
+// Kernel, layout, tables and workspace of one stored precision.
+struct Variant {
+  bool present = false;
+  ApplyKernel k{};
+  FactorLayout L{};
+  void *tabB[kMaxDim] = {nullptr, nullptr, nullptr};
+  void *tabD[kMaxDim] = {nullptr, nullptr, nullptr};
+  int T[kMaxDim] = {1, 1, 1};
+  int Qpad[kMaxDim] = {0, 0, 0};
+  int ntiles = 0;
+  size_t bytesM = 0, bytesK = 0;
+  void *vpart = nullptr;
+  size_t vpart_bytes = 0;
+  void *u_stage = nullptr, *v_stage = nullptr;
+};
+
+}  // namespace igasf
+
+struct igasf_plan {
+  int d = 0, p = 0, device = 0;
+  int N[igasf::kMaxDim] = {1, 1, 1}, K[igasf::kMaxDim] = {1, 1, 1}, Q[igasf::kMaxDim] = {1, 1, 1};
+  int64_t Ntot = 0, Qtot = 0;
+  double *knots[igasf::kMaxDim] = {nullptr, nullptr, nullptr};
+  int *span[igasf::kMaxDim] = {nullptr, nullptr, nullptr};
+  double *nodes[igasf::kMaxDim] = {nullptr, nullptr, nullptr};
+  double *weights[igasf::kMaxDim] = {nullptr, nullptr, nullptr};
+  double *tabB[igasf::kMaxDim] = {nullptr, nullptr, nullptr};  // FP64 [j][Q]
+  double *tabD[igasf::kMaxDim] = {nullptr, nullptr, nullptr};
+  int default_prec = IGASF_FP64;
+  igasf::Variant var[igasf::kNumPrec];
+  unsigned int *status = nullptr;        // device status word (bounded waits)
+  long long wait_limit = 2000000000LL;   // about one second at 2 GHz
+  int skip_slab = -1;                    // test hook, see igasf_set_test_fault
+  std::vector<cudaEvent_t> prof_events;  // 3 per timed apply
+  int prof_next = 0;                     // applies recorded so far
+  double *dinv64 = nullptr;              // inverse Jacobi diagonal of K (solver), lazily
+  float *dinv32 = nullptr;
+};

@@ -34,19 +34,20 @@ int list_apply_kernels(int d, int p, int prec, ApplyKernel *out, int max_out) {
   return 0;
 }
 
-bool find_apply_kernel(int d, int p, int prec, const int *tile, ApplyKernel *out) {
+bool find_apply_kernel(int d, int p, int prec, const int *tile, int variant, ApplyKernel *out) {
   ApplyKernel cand[kMaxCandidates];
   const int n = list_apply_kernels(d, p, prec, cand, kMaxCandidates);
   if (n == 0) return false;
   bool any = false;
   for (int a = 0; a < d; ++a) any = any || (tile && tile[a] != 0);
+  any = any || variant != 0;
   if (!any) {
     *out = cand[0];
     return true;
   }
   for (int i = 0; i < n; ++i) {
-    bool ok = true;
-    for (int a = 0; a < d; ++a)
+    bool ok = variant == 0 || variant == cand[i].variant;
+    for (int a = 0; a < d && tile; ++a)
       if (tile[a] != 0 && tile[a] != cand[i].S[a]) ok = false;
     if (ok) {
       *out = cand[i];

@@ -23,6 +23,9 @@ FP32 = 1
 COEF_CONSTANT = 0
 COEF_EXP_SIN_COS = 1
 COEF_VALUES = 2
+KERNEL_DEFAULT = 0
+KERNEL_REGISTERS = 1
+KERNEL_RING = 2
 
 ERRORS = {
     -1: "INVALID_ARG", -2: "KNOTS", -3: "GEOMETRY", -4: "UNSUPPORTED", -5: "CUDA",
@@ -34,6 +37,7 @@ EXPORTED = [
     "igasf_setup", "igasf_apply", "igasf_apply_prec", "igasf_apply_host", "igasf_destroy",
     "igasf_num_dofs", "igasf_num_quad_points", "igasf_describe", "igasf_get_tables",
     "igasf_get_factors", "igasf_profile_begin", "igasf_profile_end", "igasf_apply_noalloc",
+    "igasf_device_status", "igasf_set_test_fault", "igasf_cg_solve",
     "igasf_last_error_message", "igasf_version",
 ]
 
@@ -51,7 +55,14 @@ class Coef(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("precisions", ctypes.c_uint), ("default_prec", ctypes.c_int),
-                ("tile", ctypes.c_int * 3), ("reserved", ctypes.c_int * 8)]
+                ("tile", ctypes.c_int * 3), ("kernel_variant", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
+
+
+class CgReport(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+                ("inner_iterations", ctypes.c_int), ("final_relres", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
 
 
 class PlanDesc(ctypes.Structure):
@@ -59,7 +70,7 @@ class PlanDesc(ctypes.Structure):
                 ("tiles", ctypes.c_int * 3), ("threads_per_block", ctypes.c_int),
                 ("num_dofs", ctypes.c_int64), ("num_quad_points", ctypes.c_int64),
                 ("factor_bytes", ctypes.c_int64 * 2), ("workspace_bytes", ctypes.c_int64),
-                ("smem_bytes", ctypes.c_size_t * 2)]
+                ("smem_bytes", ctypes.c_size_t * 2), ("kernel_variant", ctypes.c_int)]
 
 
 _lib = None
@@ -90,6 +101,10 @@ def load_library(path: str = LIB_PATH):
     lib.igasf_get_tables.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp]
     lib.igasf_get_factors.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
     lib.igasf_apply_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+    lib.igasf_cg_solve.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int, ctypes.POINTER(CgReport), vp]
+    lib.igasf_device_status.argtypes = [vp, ctypes.c_int]
+    lib.igasf_set_test_fault.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
     lib.igasf_profile_begin.argtypes = [vp, ctypes.c_int]
     lib.igasf_profile_end.argtypes = [vp, dp, ip]
     lib.igasf_last_error_message.restype = ctypes.c_char_p
@@ -125,7 +140,7 @@ class Plan:
                  ctrl: np.ndarray, coef_kind: int = COEF_CONSTANT, coef_constant: float = 1.0,
                  coef_alpha: float = 0.0, coef_values: Optional[np.ndarray] = None,
                  precisions: Sequence[int] = (FP64,), default_prec: Optional[int] = None,
-                 tile: Optional[Sequence[int]] = None):
+                 tile: Optional[Sequence[int]] = None, kernel_variant: int = 0):
         lib = load_library()
         self.d = d
         self._orders = (ctypes.c_int * d)(*orders)
@@ -146,6 +161,7 @@ class Plan:
         if tile is not None:
             for i, s in enumerate(tile):
                 opt.tile[i] = int(s)
+        opt.kernel_variant = int(kernel_variant)
         h = ctypes.c_void_p()
         _check(lib.igasf_setup(d, self._orders, self._lens, self._kptrs, _dptr(self._ctrl),
                                ctypes.byref(coef), ctypes.byref(opt), ctypes.byref(h)))
@@ -199,7 +215,8 @@ class Plan:
                     num_quad_points=d.num_quad_points,
                     factor_bytes=[int(x) for x in d.factor_bytes],
                     workspace_bytes=int(d.workspace_bytes),
-                    smem_bytes=[int(x) for x in d.smem_bytes])
+                    smem_bytes=[int(x) for x in d.smem_bytes],
+                    kernel_variant=int(d.kernel_variant))
 
     def tables(self, direction: int):
         """(nodes, weights, B[Q, p], dB[Q, p]) of one direction, FP64 from the device."""
@@ -218,6 +235,25 @@ class Plan:
         out = np.zeros(self.num_quad_points * nf)
         _check(load_library().igasf_get_factors(self._h(), int(op), int(prec), _dptr(out)))
         return out.reshape(self.num_quad_points, nf) if nf > 1 else out
+
+    def cg_solve(self, b, x, inner_prec: int = FP32, rtol: float = 1e-10,
+                 inner_rtol: float = 1e-4, max_iterations: int = 200000, stream=None) -> dict:
+        """Solve K x = b (homogeneous Dirichlet) on device float64 tensors."""
+        rep = CgReport()
+        _check(load_library().igasf_cg_solve(self._h(), int(inner_prec), b.data_ptr(), x.data_ptr(),
+                                             float(rtol), float(inner_rtol), int(max_iterations),
+                                             ctypes.byref(rep), _stream_handle(stream)))
+        return dict(converged=bool(rep.converged), outer_iterations=rep.outer_iterations,
+                    inner_iterations=rep.inner_iterations, final_relres=rep.final_relres,
+                    seconds=rep.seconds)
+
+    def device_status(self, clear: bool = True) -> int:
+        """IGASF_OK (0) or IGASF_ERR_TIMEOUT (-7) if a bounded device wait ran out."""
+        return int(load_library().igasf_device_status(self._h(), int(clear)))
+
+    def set_test_fault(self, skip_slab: int = -1, wait_limit_cycles: int = 2000000000):
+        _check(load_library().igasf_set_test_fault(self._h(), int(skip_slab),
+                                                   int(wait_limit_cycles)))
 
     def profile_begin(self, max_applies: int):
         _check(load_library().igasf_profile_begin(self._h(), int(max_applies)))

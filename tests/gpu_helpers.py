@@ -19,6 +19,7 @@ def gpu_apply(plan, op, u, prec):
     vd = torch.empty_like(ud)
     plan.apply(op, ud, vd, prec=prec)
     torch.cuda.synchronize()
+    assert plan.device_status() == 0, "a bounded device wait ran out"
     return vd.double().cpu().numpy()
 
 

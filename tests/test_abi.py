@@ -145,6 +145,9 @@ def test_null_handle_calls(lib):
     assert lib.igasf_describe(None, 0, None) == -1
     assert lib.igasf_get_tables(None, 0, None, None, None, None) == -1
     assert lib.igasf_get_factors(None, 0, 0, None) == -1
+    assert lib.igasf_device_status(None, 0) == -1
+    assert lib.igasf_set_test_fault(None, 0, 100000) == -1
+    assert lib.igasf_cg_solve(None, 1, None, None, 1e-10, 1e-4, 10, None, None) == -1
 
 
 def test_binding_raises_without_library(tmp_path):

@@ -1,0 +1,63 @@
+"""Jacobi-PCG and mixed-precision iterative refinement (GPU) against a direct
+solve of the oracle's assembled stiffness matrix (homogeneous Dirichlet: the
+interior block K_II), and against each other."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle as O
+from paper_1809_05471_gb300 import igasf as G
+from paper_1809_05471_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _interior_mask(patch):
+    Ns = patch.dofs_per_dir
+    idx = np.arange(patch.num_dofs)
+    i0, i1, i2 = idx % Ns[0], (idx // Ns[0]) % Ns[1], idx // (Ns[0] * Ns[1])
+    return (i0 > 0) & (i0 < Ns[0] - 1) & (i1 > 0) & (i1 < Ns[1] - 1) & (i2 > 0) & (i2 < Ns[2] - 1)
+
+
+@pytest.mark.parametrize("p,K", [(3, 6), (4, 5)])
+def test_cg_matches_direct_interior_solve(p, K):
+    import torch
+    patch, u = I.config_cube(p=p, K=K)
+    rp, ci, va = O.assemble_csr(patch, O.STIFFNESS)
+    A = sp.csr_matrix((va, ci, rp), shape=(patch.num_dofs,) * 2)
+    m = _interior_mask(patch)
+    rng = np.random.default_rng(4)
+    b = rng.uniform(-1, 1, patch.num_dofs)
+    b[~m] = 0.0
+    x_ref = np.zeros(patch.num_dofs)
+    x_ref[m] = spla.spsolve(A[m][:, m].tocsc(), b[m])
+    with G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32)) as plan:
+        bd = torch.as_tensor(b, device="cuda")
+        for inner in (G.FP64, G.FP32):
+            xd = torch.zeros_like(bd)
+            rep = plan.cg_solve(bd, xd, inner_prec=inner, rtol=1e-11, inner_rtol=1e-4)
+            x = xd.cpu().numpy()
+            assert rep["converged"], rep
+            assert rep["final_relres"] <= 1e-11
+            assert np.all(x[~m] == 0.0)
+            # residual of the oracle's matrix at the GPU solution
+            res = np.linalg.norm((A[m][:, m] @ x[m]) - b[m]) / np.linalg.norm(b[m])
+            assert res < 1e-10, (inner, res)
+            assert np.max(np.abs(x - x_ref)) < 1e-7 * np.max(np.abs(x_ref)), inner
+            if inner == G.FP32:
+                assert rep["outer_iterations"] >= 2
+
+
+def test_cg_is_deterministic_and_reports_non_convergence():
+    import torch
+    patch, u = I.config_cube(p=3, K=8)
+    with G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32)) as plan:
+        b = torch.as_tensor(u, device="cuda")
+        x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+        r1 = plan.cg_solve(b, x1, inner_prec=G.FP32, rtol=1e-10)
+        r2 = plan.cg_solve(b, x2, inner_prec=G.FP32, rtol=1e-10)
+        assert torch.equal(x1, x2) and r1["inner_iterations"] == r2["inner_iterations"]
+        x3 = torch.zeros_like(b)
+        r3 = plan.cg_solve(b, x3, inner_prec=G.FP64, rtol=1e-10, max_iterations=3)
+        assert not r3["converged"] and r3["inner_iterations"] == 3
