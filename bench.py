@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--solve", action="store_true",
                     help="time the Dirichlet solve (p=5, 96^3 elements) instead of the apply")
     ap.add_argument("--solve-elements", type=int, default=96)
+    ap.add_argument("--batch", action="store_true",
+                    help="time the 256-patch batched apply (seed 7) instead of the single patch")
     return ap.parse_args()
 
 
@@ -407,6 +409,80 @@ def run_solve(args):
     }), flush=True)
 
 
+def run_batch(args):
+    """256 independent d=3 patches (seed 7; 8..48 elements per direction, p = 2..6,
+    constant a ~ U[0.5, 2]), FP32 stiffness, applied as one CUDA graph launch.
+    Tile shape and kernel variant per order come from the library autotuner run on
+    the largest patch of that order."""
+    import numpy as np
+    import torch
+
+    from paper_1809_05471_gb300 import igasf as G
+    from paper_1809_05471_gb300 import inputs as I
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    patches = I.config_batch()
+    t0 = time.perf_counter()
+    tuned = {}
+    for p in sorted({pt.orders[0] for pt, _ in patches}):
+        big = max((pt for pt, _ in patches if pt.orders[0] == p), key=lambda q: q.num_quad_points)
+        tile, variant, ms = G.autotune(big, op=G.STIFFNESS, prec=G.FP32, repeats=5)
+        tuned[p] = {"tile": tile, "variant": variant, "ms_on_largest": round(ms, 4)}
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plans = [G.Plan.from_patch(pt, precisions=(G.FP32,), tile=tuned[pt.orders[0]]["tile"],
+                               kernel_variant=tuned[pt.orders[0]]["variant"]) for pt, _ in patches]
+    setup_s = time.perf_counter() - t0
+    u = np.concatenate([u for _, u in patches])
+    ud = torch.as_tensor(u, device="cuda").float()
+    vd = torch.empty_like(ud)
+    batch = G.Batch(plans, op=G.STIFFNESS, prec=G.FP32)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup // 10)):
+        batch.apply(ud, vd, stream=stream)
+    steps = max(10, args.steps // 20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        batch.apply(ud, vd, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # the same work as individual applies, one after another (no graph)
+    e0.record(stream)
+    for _ in range(3):
+        for k, plan in enumerate(plans):
+            a, b = int(batch.offsets[k]), int(batch.offsets[k + 1])
+            plan.apply(G.STIFFNESS, ud[a:b], vd[a:b], prec=G.FP32, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1) / 3
+    peaks, _ = measured_peaks()
+    alg = 24 * batch.total_quad_points + 8 * batch.total_dofs
+    ok = all(plan.device_status() == 0 for plan in plans)
+    print(json.dumps({
+        "metric": "batched 3D stiffness apply GDoF/s (256 uneven patches, one graph launch)",
+        "value": round(batch.total_dofs / (ms * 1e-3) / 1e9, 4), "unit": "GDoF/s", "n_gpus": 1,
+        "steps": steps, "ms_per_step": round(ms, 4), "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "256 patches from seed 7: 8..48 elements per direction, p = 2..6, "
+                               "a ~ U[0.5, 2]; %d dofs, %d quadrature points" % (batch.total_dofs,
+                                                                                batch.total_quad_points),
+                   "launch_groups": batch.launch_groups, "tuned": {str(k): v for k, v in tuned.items()}},
+        "roofline": {"bound": "hbm", "achieved": round(alg / (ms * 1e-3) / 1e9, 1),
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                     "note": "whole graph (tile kernels + gather), algorithmic bytes 24 B/qp + 8 B/dof"},
+        "sequential_individual_applies_ms": round(ms_seq, 4),
+        "autotune_s": round(tune_s, 2), "setup_s": round(setup_s, 2),
+        "device_status": "ok" if ok else "a bounded wait ran out",
+    }), flush=True)
+    batch.close()
+    for plan in plans:
+        plan.close()
+
+
 def run_reference(args):
     """The oracle as it stands, on the host cores, on the same workload and metric:
     each step computes a bounded sample of rows of v = A u."""
@@ -457,6 +533,8 @@ def main():
         run_reference(args)
     elif args.solve:
         run_solve(args)
+    elif args.batch:
+        run_batch(args)
     else:
         run_igasf(args)
 

@@ -281,6 +281,43 @@ typedef struct {
 int igasf_cg_solve(igasf_handle h, int inner_prec, const double *b, double *x, double rtol,
                    double inner_rtol, int max_iterations, igasf_cg_report *report, void *stream);
 
+/*
+ * Many independent 3D patches applied together (the multipatch setting of
+ * Sec. 4, Example multipatch, with the patches kept independent: no interface
+ * gluing). igasf_batch_create takes already set-up plans (which must outlive
+ * the batch and must not be applied on their own while a batch apply may be
+ * running: they share their workspace with it), groups them by tile kernel
+ * (order, tile shape, factor-stream variant) and captures one launch per group
+ * plus one gather for all patches into a CUDA graph. igasf_batch_apply then
+ * applies every patch's operator `op` in precision `prec` with one graph
+ * launch on `stream`:
+ *   u, v: device arrays holding the patches' vectors back to back in plan
+ *         order (patch i starts at the sum of num_dofs of patches 0..i-1),
+ *         element type of `prec`, not overlapping. v is overwritten.
+ * The first apply with a given (u, v), and every change of them, uploads the
+ * per-patch pointer tables (a short synchronous copy). Results equal the
+ * patches' individual applies bit for bit. Errors: INVALID_ARG, UNSUPPORTED
+ * (a plan lacks `prec`, or is 2D), CUDA, OOM.
+ */
+typedef struct igasf_batch_s *igasf_batch;
+int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, igasf_batch *out);
+int igasf_batch_apply(igasf_batch b, const void *u, void *v, void *stream);
+int igasf_batch_info(igasf_batch b, int64_t *total_dofs, int64_t *total_quad_points,
+                     int64_t *factor_bytes, int *launch_groups);
+int igasf_batch_destroy(igasf_batch b);
+
+/*
+ * Tile autotuner: sets the given patch up with every compiled (tile shape,
+ * factor-stream variant) candidate of its order for `prec`, times `repeats`
+ * applies of `op` of each with CUDA events (after two warm-up applies), and
+ * returns the fastest candidate in tile[3] (1 in unused directions) and
+ * *kernel_variant, and its time per apply in *best_ms (may be NULL). Patch
+ * arguments as for igasf_setup. Synchronous; allocates temporarily.
+ */
+int igasf_autotune(int d, const int *orders, const int *knot_lengths, const double *const *knots,
+                   const double *ctrl, const igasf_coef *coef, int op, int prec, int repeats,
+                   int *tile, int *kernel_variant, double *best_ms);
+
 /* Message for the last error on this host thread ("" if none). */
 const char *igasf_last_error_message(void);
 

@@ -200,6 +200,8 @@ ApplyKernel make_apply2d() {
   k.variant = IGASF_KERNEL_REGISTERS;
   k.launch[IGASF_MASS] = &launch_apply2d<T, P, S1, S2, false>;
   k.launch[IGASF_STIFFNESS] = &launch_apply2d<T, P, S1, S2, true>;
+  k.launch_batched[IGASF_MASS] = nullptr;
+  k.launch_batched[IGASF_STIFFNESS] = nullptr;
   k.prepare = &prepare_apply2d<T, P, S1, S2>;
   return k;
 }

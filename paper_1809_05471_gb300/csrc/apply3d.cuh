@@ -46,8 +46,7 @@ template <typename T>
 __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
 
 template <typename T, int P, int S1, int S2, int S3, bool STIFF>
-__global__ void __launch_bounds__(Tile3<P, S1, S2, S3>::NT)
-apply3d_kernel(const ApplyParams prm) {
+__device__ __forceinline__ void apply3d_body(const ApplyParams &prm, const int tile) {
   using G = Tile3<P, S1, S2, S3>;
   constexpr int E1 = G::E1, E2 = G::E2, E3 = G::E3;
   constexpr int Q1 = G::Q1, Q2 = G::Q2, Q3 = G::Q3;
@@ -66,7 +65,6 @@ apply3d_kernel(const ApplyParams prm) {
   T *Y1 = Y0 + G::Y, *Y2 = Y1 + G::Y;       // stiffness only
 
   const int tid = threadIdx.x;
-  const int tile = blockIdx.x;
   const int t1 = tile % prm.T[0];
   const int t2 = (tile / prm.T[0]) % prm.T[1];
   const int t3 = tile / (prm.T[0] * prm.T[1]);
@@ -275,6 +273,21 @@ apply3d_kernel(const ApplyParams prm) {
 }
 
 template <typename T, int P, int S1, int S2, int S3, bool STIFF>
+__global__ void __launch_bounds__(Tile3<P, S1, S2, S3>::NT)
+apply3d_kernel(const ApplyParams prm) {
+  apply3d_body<T, P, S1, S2, S3, STIFF>(prm, blockIdx.x);
+}
+
+// Many patches in one launch: block b works on tile b - first_block[patch] of
+// patch = block_patch[b], with that patch's parameters.
+template <typename T, int P, int S1, int S2, int S3, bool STIFF>
+__global__ void __launch_bounds__(Tile3<P, S1, S2, S3>::NT)
+apply3d_batched(const BatchParams bp) {
+  const int patch = bp.block_patch[blockIdx.x];
+  apply3d_body<T, P, S1, S2, S3, STIFF>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
+}
+
+template <typename T, int P, int S1, int S2, int S3, bool STIFF>
 cudaError_t launch_apply3d(const ApplyParams &prm, cudaStream_t s) {
   using G = Tile3<P, S1, S2, S3>;
   const size_t smem = G::smem_words(STIFF) * sizeof(T);
@@ -289,9 +302,24 @@ cudaError_t prepare_apply3d() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(G::smem_words(false) * sizeof(T)));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(apply3d_kernel<T, P, S1, S2, S3, true>,
+  e = cudaFuncSetAttribute(apply3d_kernel<T, P, S1, S2, S3, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(G::smem_words(true) * sizeof(T)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(apply3d_batched<T, P, S1, S2, S3, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(G::smem_words(false) * sizeof(T)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(apply3d_batched<T, P, S1, S2, S3, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(G::smem_words(true) * sizeof(T)));
+}
+
+template <typename T, int P, int S1, int S2, int S3, bool STIFF>
+cudaError_t launch_apply3d_batched(const BatchParams &bp, int blocks, cudaStream_t s) {
+  using G = Tile3<P, S1, S2, S3>;
+  apply3d_batched<T, P, S1, S2, S3, STIFF><<<blocks, G::NT, G::smem_words(STIFF) * sizeof(T), s>>>(bp);
+  return cudaGetLastError();
 }
 
 template <typename T, int P, int S1, int S2, int S3>
@@ -311,6 +339,8 @@ ApplyKernel make_apply3d() {
   k.variant = IGASF_KERNEL_REGISTERS;
   k.launch[IGASF_MASS] = &launch_apply3d<T, P, S1, S2, S3, false>;
   k.launch[IGASF_STIFFNESS] = &launch_apply3d<T, P, S1, S2, S3, true>;
+  k.launch_batched[IGASF_MASS] = &launch_apply3d_batched<T, P, S1, S2, S3, false>;
+  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_batched<T, P, S1, S2, S3, true>;
   k.prepare = &prepare_apply3d<T, P, S1, S2, S3>;
   return k;
 }

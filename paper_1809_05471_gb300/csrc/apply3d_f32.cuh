@@ -123,8 +123,7 @@ struct TileF2 {
 };
 
 template <int P, int S1, int S2, int S3, bool STIFF>
-__global__ void __launch_bounds__(TileF2<P, S1, S2, S3>::NT)
-apply3d_f32_kernel(const ApplyParams prm) {
+__device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const int tile) {
   using G = TileF2<P, S1, S2, S3>;
   constexpr int E1 = G::E1, E2 = G::E2, E3 = G::E3;
   constexpr int Q1 = G::Q1, Q2 = G::Q2, Q3 = G::Q3;
@@ -149,7 +148,6 @@ apply3d_f32_kernel(const ApplyParams prm) {
   float *us = reinterpret_cast<float *>(STIFF ? Y2 + G::Y / 2 : Y0 + G::Y / 2);
 
   const int tid = threadIdx.x;
-  const int tile = blockIdx.x;
   const int t1 = tile % prm.T[0];
   const int t2 = (tile / prm.T[0]) % prm.T[1];
   const int t3 = tile / (prm.T[0] * prm.T[1]);
@@ -479,21 +477,44 @@ apply3d_f32_kernel(const ApplyParams prm) {
 }
 
 template <int P, int S1, int S2, int S3, bool STIFF>
+__global__ void __launch_bounds__(TileF2<P, S1, S2, S3>::NT)
+apply3d_f32_kernel(const ApplyParams prm) {
+  apply3d_f32_body<P, S1, S2, S3, STIFF>(prm, blockIdx.x);
+}
+
+// Many patches in one launch: block b works on tile b - first_block[patch] of
+// patch = block_patch[b], with that patch's parameters.
+template <int P, int S1, int S2, int S3, bool STIFF>
+__global__ void __launch_bounds__(TileF2<P, S1, S2, S3>::NT)
+apply3d_f32_batched(const BatchParams bp) {
+  const int patch = bp.block_patch[blockIdx.x];
+  apply3d_f32_body<P, S1, S2, S3, STIFF>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
+}
+
+template <int P, int S1, int S2, int S3, bool STIFF>
 cudaError_t launch_apply3d_f32(const ApplyParams &prm, cudaStream_t s) {
   using G = TileF2<P, S1, S2, S3>;
   apply3d_f32_kernel<P, S1, S2, S3, STIFF><<<prm.ntiles, G::NT, G::smem_bytes(STIFF), s>>>(prm);
   return cudaGetLastError();
 }
 
+template <int P, int S1, int S2, int S3, bool STIFF>
+cudaError_t launch_apply3d_f32_batched(const BatchParams &bp, int blocks, cudaStream_t s) {
+  using G = TileF2<P, S1, S2, S3>;
+  apply3d_f32_batched<P, S1, S2, S3, STIFF><<<blocks, G::NT, G::smem_bytes(STIFF), s>>>(bp);
+  return cudaGetLastError();
+}
+
 template <int P, int S1, int S2, int S3>
 cudaError_t prepare_apply3d_f32() {
   using G = TileF2<P, S1, S2, S3>;
-  cudaError_t e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)G::smem_bytes(false));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, true>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes(true));
+  const int sm = (int)G::smem_bytes(false), sk = (int)G::smem_bytes(true);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, false>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, true>, a, sk);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_batched<P, S1, S2, S3, false>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_batched<P, S1, S2, S3, true>, a, sk);
+  return e;
 }
 
 template <int P, int S1, int S2, int S3>
@@ -514,6 +535,8 @@ ApplyKernel make_apply3d_f32() {
   k.variant = IGASF_KERNEL_RING;
   k.launch[IGASF_MASS] = &launch_apply3d_f32<P, S1, S2, S3, false>;
   k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32<P, S1, S2, S3, true>;
+  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32_batched<P, S1, S2, S3, false>;
+  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32_batched<P, S1, S2, S3, true>;
   k.prepare = &prepare_apply3d_f32<P, S1, S2, S3>;
   return k;
 }

@@ -70,8 +70,7 @@ struct TileF2R {
 };
 
 template <int P, int S1, int S2, int S3, bool STIFF, int PD>
-__global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
-apply3d_f32r_kernel(const ApplyParams prm) {
+__device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const int tile) {
   using G = TileF2R<P, S1, S2, S3>;
   constexpr int E1 = G::E1, E2 = G::E2, E3 = G::E3;
   constexpr int Q1 = G::Q1, Q2 = G::Q2, Q3 = G::Q3;
@@ -90,7 +89,6 @@ apply3d_f32r_kernel(const ApplyParams prm) {
   float *us = reinterpret_cast<float *>(STIFF ? Y2 + G::Y / 2 : Y0 + G::Y / 2);
 
   const int tid = threadIdx.x;
-  const int tile = blockIdx.x;
   const int t1 = tile % prm.T[0];
   const int t2 = (tile / prm.T[0]) % prm.T[1];
   const int t3 = tile / (prm.T[0] * prm.T[1]);
@@ -399,6 +397,21 @@ apply3d_f32r_kernel(const ApplyParams prm) {
 }
 
 template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+__global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
+apply3d_f32r_kernel(const ApplyParams prm) {
+  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD>(prm, blockIdx.x);
+}
+
+// Many patches in one launch: block b works on tile b - first_block[patch] of
+// patch = block_patch[b], with that patch's parameters.
+template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+__global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
+apply3d_f32r_batched(const BatchParams bp) {
+  const int patch = bp.block_patch[blockIdx.x];
+  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
+}
+
+template <int P, int S1, int S2, int S3, bool STIFF, int PD>
 cudaError_t launch_apply3d_f32r(const ApplyParams &prm, cudaStream_t s) {
   using G = TileF2R<P, S1, S2, S3>;
   apply3d_f32r_kernel<P, S1, S2, S3, STIFF, PD>
@@ -406,16 +419,25 @@ cudaError_t launch_apply3d_f32r(const ApplyParams &prm, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+cudaError_t launch_apply3d_f32r_batched(const BatchParams &bp, int blocks, cudaStream_t s) {
+  using G = TileF2R<P, S1, S2, S3>;
+  apply3d_f32r_batched<P, S1, S2, S3, STIFF, PD>
+      <<<blocks, G::NT, G::smem_floats(STIFF) * sizeof(float), s>>>(bp);
+  return cudaGetLastError();
+}
+
 template <int P, int S1, int S2, int S3, int PD>
 cudaError_t prepare_apply3d_f32r() {
   using G = TileF2R<P, S1, S2, S3>;
-  cudaError_t e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, false, PD>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(G::smem_floats(false) * sizeof(float)));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, true, PD>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(G::smem_floats(true) * sizeof(float)));
+  const int sm = (int)(G::smem_floats(false) * sizeof(float));
+  const int sk = (int)(G::smem_floats(true) * sizeof(float));
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, false, PD>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, true, PD>, a, sk);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, false, PD>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, true, PD>, a, sk);
+  return e;
 }
 
 template <int P, int S1, int S2, int S3, int PD = 2>
@@ -435,6 +457,8 @@ ApplyKernel make_apply3d_f32r() {
   k.variant = IGASF_KERNEL_REGISTERS;
   k.launch[IGASF_MASS] = &launch_apply3d_f32r<P, S1, S2, S3, false, PD>;
   k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32r<P, S1, S2, S3, true, PD>;
+  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, false, PD>;
+  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, true, PD>;
   k.prepare = &prepare_apply3d_f32r<P, S1, S2, S3, PD>;
   return k;
 }

@@ -1,0 +1,399 @@
+// Many independent patches applied as one CUDA graph, and the tile autotuner.
+//
+// A batch groups its patches by tile kernel (order, tile shape, factor-stream
+// variant). Each group is one launch of that kernel's batched wrapper, whose
+// blocks map to (patch, tile) through device tables; one batched gather then
+// sums the per-tile partial results of every patch. The launches are captured
+// once into a CUDA graph, so one batch apply is one graph launch. Per-tile
+// results and the gather's summation order are those of the single-patch
+// apply, so a batch apply equals the patches' individual applies bit for bit.
+//
+// The autotuner sets a patch up with every compiled (tile, variant) candidate
+// for its order and precision, times a few applies of each with CUDA events,
+// and returns the fastest (the paper's macro-element shape study, Sec. 7, made
+// empirical per order and patch shape).
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "igasf.h"
+#include "igasf_internal.h"
+#include "plan.h"
+
+namespace igasf {
+
+int set_error(int code, const char *msg);
+
+namespace {
+
+struct GatherParams {
+  const void *vpart;
+  void *v;
+  int N0, N1, Ntot;
+  int T0, T1, T2, S0, S1, S2, E0, E1, E2, vol;
+  int two;   // at most two tiles per direction contain a dof
+};
+
+__device__ __forceinline__ void tile_range_b(int i, int S, int E, int T, int &lo, int &hi) {
+  lo = i - E + 1 > 0 ? (i - E + S) / S : 0;
+  hi = min(T - 1, i / S);
+}
+
+// Same arithmetic and summation order as the single-patch gather.
+template <typename T>
+__global__ void batched_gather_kernel(const GatherParams *gp, const int *block_patch,
+                                      const int *first_block) {
+  const int patch = block_patch[blockIdx.x];
+  const GatherParams g = gp[patch];
+  const int n = (blockIdx.x - first_block[patch]) * blockDim.x + threadIdx.x;
+  if (n >= g.Ntot) return;
+  const T *vpart = static_cast<const T *>(g.vpart);
+  const int i0 = n % g.N0, r = n / g.N0;
+  const int i1 = r % g.N1, i2 = r / g.N1;
+  int lo0, hi0, lo1, hi1, lo2, hi2;
+  tile_range_b(i0, g.S0, g.E0, g.T0, lo0, hi0);
+  tile_range_b(i1, g.S1, g.E1, g.T1, lo1, hi1);
+  tile_range_b(i2, g.S2, g.E2, g.T2, lo2, hi2);
+  T acc = T(0);
+  if (g.two) {
+    T x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int t2 = lo2 + (c >> 2), t1 = lo1 + ((c >> 1) & 1), t0 = lo0 + (c & 1);
+      x[c] = T(0);
+      if (t2 <= hi2 && t1 <= hi1 && t0 <= hi0) {
+        const int64_t tile = ((int64_t)t2 * g.T1 + t1) * g.T0 + t0;
+        const int loc = ((i2 - t2 * g.S2) * g.E1 + (i1 - t1 * g.S1)) * g.E0 + (i0 - t0 * g.S0);
+        x[c] = vpart[tile * g.vol + loc];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc += x[c];
+  } else {
+    for (int t2 = lo2; t2 <= hi2; ++t2)
+      for (int t1 = lo1; t1 <= hi1; ++t1)
+        for (int t0 = lo0; t0 <= hi0; ++t0) {
+          const int64_t tile = ((int64_t)t2 * g.T1 + t1) * g.T0 + t0;
+          const int loc = ((i2 - t2 * g.S2) * g.E1 + (i1 - t1 * g.S1)) * g.E0 + (i0 - t0 * g.S0);
+          acc += vpart[tile * g.vol + loc];
+        }
+  }
+  static_cast<T *>(g.v)[n] = acc;
+}
+
+constexpr int kGatherThreads = 256;
+
+}  // namespace
+}  // namespace igasf
+
+struct igasf_batch_s {
+  int n = 0, op = 0, prec = 0;
+  std::vector<igasf_plan *> plans;
+  std::vector<int64_t> offset;             // first dof of each patch in packed u, v
+  int64_t total_dofs = 0, total_qp = 0, factor_bytes = 0;
+  struct Group {
+    igasf::ApplyKernel k{};
+    std::vector<int> patches;
+    int blocks = 0;
+    std::vector<igasf::ApplyParams> h_params;
+    igasf::ApplyParams *d_params = nullptr;
+    int *d_block_patch = nullptr, *d_first_block = nullptr;
+  };
+  std::vector<Group> groups;
+  std::vector<igasf::GatherParams> h_gp;
+  igasf::GatherParams *d_gp = nullptr;
+  int *d_gblock_patch = nullptr, *d_gfirst = nullptr;
+  int gblocks = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void *last_u = nullptr;
+  void *last_v = nullptr;
+};
+
+namespace {
+
+void free_batch(igasf_batch b) {
+  if (!b) return;
+  for (auto &g : b->groups) {
+    cudaFree(g.d_params);
+    cudaFree(g.d_block_patch);
+    cudaFree(g.d_first_block);
+  }
+  cudaFree(b->d_gp);
+  cudaFree(b->d_gblock_patch);
+  cudaFree(b->d_gfirst);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+template <typename V>
+cudaError_t upload(V **dst, const std::vector<V> &src) {
+  cudaError_t e = cudaMalloc((void **)dst, sizeof(V) * (src.empty() ? 1 : src.size()));
+  if (e == cudaSuccess && !src.empty())
+    e = cudaMemcpy(*dst, src.data(), sizeof(V) * src.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Point the per-patch parameters at packed u and v and upload them.
+cudaError_t bind_vectors(igasf_batch b, const void *u, void *v) {
+  const size_t es = b->prec == IGASF_FP64 ? 8 : 4;
+  cudaError_t e = cudaSuccess;
+  for (auto &g : b->groups) {
+    for (size_t i = 0; i < g.patches.size(); ++i)
+      g.h_params[i].u = static_cast<const char *>(u) + es * b->offset[g.patches[i]];
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g.d_params, g.h_params.data(), sizeof(igasf::ApplyParams) * g.h_params.size(),
+                     cudaMemcpyHostToDevice);
+  }
+  for (int i = 0; i < b->n; ++i) b->h_gp[i].v = static_cast<char *>(v) + es * b->offset[i];
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_gp, b->h_gp.data(), sizeof(igasf::GatherParams) * b->h_gp.size(),
+                   cudaMemcpyHostToDevice);
+  b->last_u = u;
+  b->last_v = v;
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, igasf_batch *out) {
+  using namespace igasf;
+  if (!out || !plans || nplans < 1) return set_error(IGASF_ERR_INVALID_ARG, "need nplans >= 1, plans and out");
+  if (op != IGASF_MASS && op != IGASF_STIFFNESS) return set_error(IGASF_ERR_INVALID_ARG, "bad op");
+  if (prec != IGASF_FP64 && prec != IGASF_FP32) return set_error(IGASF_ERR_INVALID_ARG, "bad prec");
+  for (int i = 0; i < nplans; ++i) {
+    const igasf_plan *h = plans[i];
+    if (!h) return set_error(IGASF_ERR_INVALID_ARG, "a plan is NULL");
+    if (!h->var[prec].present) return set_error(IGASF_ERR_UNSUPPORTED, "a plan lacks the batch precision");
+    if (!h->var[prec].k.launch_batched[op])
+      return set_error(IGASF_ERR_UNSUPPORTED, "a plan's kernel has no batched form (2D plans)");
+  }
+  igasf_batch b = new (std::nothrow) igasf_batch_s();
+  if (!b) return set_error(IGASF_ERR_OOM, "host allocation");
+  b->n = nplans;
+  b->op = op;
+  b->prec = prec;
+  b->plans.assign(plans, plans + nplans);
+  b->offset.resize(nplans);
+  b->h_gp.resize(nplans);
+  int64_t off = 0;
+  for (int i = 0; i < nplans; ++i) {
+    igasf_plan *h = b->plans[i];
+    const Variant &v = h->var[prec];
+    b->offset[i] = off;
+    off += h->Ntot;
+    b->total_qp += h->Qtot;
+    b->factor_bytes += op == IGASF_MASS ? v.bytesM : v.bytesK;
+    // group by kernel
+    int gi = -1;
+    for (size_t g = 0; g < b->groups.size(); ++g)
+      if (b->groups[g].k.launch_batched[op] == v.k.launch_batched[op]) gi = (int)g;
+    if (gi < 0) {
+      b->groups.emplace_back();
+      gi = (int)b->groups.size() - 1;
+      b->groups[gi].k = v.k;
+    }
+    auto &G = b->groups[gi];
+    G.patches.push_back(i);
+    ApplyParams prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.vpart = v.vpart;
+    prm.D = op == IGASF_MASS ? v.L.DM : v.L.DK;
+    for (int a = 0; a < kMaxDim; ++a) {
+      prm.tabB[a] = v.tabB[a];
+      prm.tabD[a] = v.tabD[a];
+      prm.N[a] = h->N[a];
+      prm.K[a] = h->K[a];
+      prm.T[a] = v.T[a];
+      prm.Qpad[a] = v.Qpad[a];
+    }
+    prm.ntiles = v.ntiles;
+    prm.status = h->status;
+    prm.wait_limit = h->wait_limit;
+    prm.skip_slab = -1;
+    G.h_params.push_back(prm);
+    GatherParams &gp = b->h_gp[i];
+    gp.vpart = v.vpart;
+    gp.N0 = h->N[0];
+    gp.N1 = h->N[1];
+    gp.Ntot = (int)h->Ntot;
+    gp.T0 = v.T[0];
+    gp.T1 = v.T[1];
+    gp.T2 = v.T[2];
+    gp.S0 = v.k.S[0];
+    gp.S1 = v.k.S[1];
+    gp.S2 = v.k.S[2];
+    gp.E0 = gp.S0 + h->p - 1;
+    gp.E1 = gp.S1 + h->p - 1;
+    gp.E2 = gp.S2 + h->p - 1;
+    gp.vol = gp.E0 * gp.E1 * gp.E2;
+    gp.two = gp.E0 <= 2 * gp.S0 && gp.E1 <= 2 * gp.S1 && gp.E2 <= 2 * gp.S2;
+  }
+  b->total_dofs = off;
+  // device tables
+  cudaError_t e = cudaSuccess;
+  for (auto &G : b->groups) {
+    std::vector<int> bp;
+    std::vector<int> local_first(G.patches.size());
+    for (size_t j = 0; j < G.patches.size(); ++j) {
+      local_first[j] = (int)bp.size();
+      for (int t = 0; t < G.h_params[j].ntiles; ++t) bp.push_back((int)j);
+    }
+    G.blocks = (int)bp.size();
+    if (e == cudaSuccess) e = upload(&G.d_block_patch, bp);
+    if (e == cudaSuccess) e = upload(&G.d_first_block, local_first);
+    if (e == cudaSuccess) e = upload(&G.d_params, G.h_params);
+  }
+  {
+    std::vector<int> bp, first(b->n);
+    for (int i = 0; i < b->n; ++i) {
+      first[i] = (int)bp.size();
+      const int nb = (b->h_gp[i].Ntot + kGatherThreads - 1) / kGatherThreads;
+      for (int k = 0; k < nb; ++k) bp.push_back(i);
+    }
+    b->gblocks = (int)bp.size();
+    if (e == cudaSuccess) e = upload(&b->d_gblock_patch, bp);
+    if (e == cudaSuccess) e = upload(&b->d_gfirst, first);
+    if (e == cudaSuccess) e = upload(&b->d_gp, b->h_gp);
+  }
+  // capture the launches into a graph
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (auto &G : b->groups) {
+      BatchParams bp;
+      bp.params = G.d_params;
+      bp.block_patch = G.d_block_patch;
+      bp.first_block = G.d_first_block;
+      const cudaError_t le = G.k.launch_batched[op](bp, G.blocks, b->cap);
+      if (le != cudaSuccess && e == cudaSuccess) e = le;
+    }
+    if (prec == IGASF_FP32)
+      batched_gather_kernel<float><<<b->gblocks, kGatherThreads, 0, b->cap>>>(b->d_gp, b->d_gblock_patch,
+                                                                            b->d_gfirst);
+    else
+      batched_gather_kernel<double><<<b->gblocks, kGatherThreads, 0, b->cap>>>(b->d_gp, b->d_gblock_patch,
+                                                                             b->d_gfirst);
+    const cudaError_t ce = cudaStreamEndCapture(b->cap, &b->graph);
+    if (e == cudaSuccess) e = ce;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return set_error(e == cudaErrorMemoryAllocation ? IGASF_ERR_OOM : IGASF_ERR_CUDA,
+                     (std::string("batch set-up: ") + cudaGetErrorString(e)).c_str());
+  }
+  *out = b;
+  return IGASF_OK;
+}
+
+int igasf_batch_apply(igasf_batch b, const void *u, void *v, void *stream) {
+  using namespace igasf;
+  if (!b || !u || !v) return set_error(IGASF_ERR_INVALID_ARG, "batch, u and v must be non-NULL");
+  const size_t es = b->prec == IGASF_FP64 ? 8 : 4;
+  if (((uintptr_t)u % es) || ((uintptr_t)v % es))
+    return set_error(IGASF_ERR_INVALID_ARG, "u and v must be aligned to the element size");
+  const uintptr_t ub = (uintptr_t)u, vb = (uintptr_t)v, len = (uintptr_t)b->total_dofs * es;
+  if (ub < vb + len && vb < ub + len) return set_error(IGASF_ERR_INVALID_ARG, "u and v overlap");
+  cudaError_t e = cudaSuccess;
+  if (u != b->last_u || v != b->last_v) {
+    e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));   // earlier launches read the old tables
+    if (e == cudaSuccess) e = bind_vectors(b, u, v);
+  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return set_error(IGASF_ERR_CUDA, (std::string("batch apply: ") + cudaGetErrorString(e)).c_str());
+  return IGASF_OK;
+}
+
+int igasf_batch_info(igasf_batch b, int64_t *total_dofs, int64_t *total_quad_points,
+                     int64_t *factor_bytes, int *launch_groups) {
+  if (!b) return igasf::set_error(IGASF_ERR_INVALID_ARG, "batch is NULL");
+  if (total_dofs) *total_dofs = b->total_dofs;
+  if (total_quad_points) *total_quad_points = b->total_qp;
+  if (factor_bytes) *factor_bytes = b->factor_bytes;
+  if (launch_groups) *launch_groups = (int)b->groups.size();
+  return IGASF_OK;
+}
+
+int igasf_batch_destroy(igasf_batch b) {
+  if (!b) return IGASF_OK;
+  const cudaError_t e = cudaDeviceSynchronize();
+  free_batch(b);
+  if (e != cudaSuccess) return igasf::set_error(IGASF_ERR_CUDA, cudaGetErrorString(e));
+  return IGASF_OK;
+}
+
+}  // extern "C"
+
+extern "C" int igasf_autotune(int d, const int *orders, const int *knot_lengths,
+                              const double *const *knots, const double *ctrl, const igasf_coef *coef,
+                              int op, int prec, int repeats, int *tile, int *kernel_variant,
+                              double *best_ms) {
+  using namespace igasf;
+  if (!tile || !kernel_variant || !orders || repeats < 1)
+    return set_error(IGASF_ERR_INVALID_ARG, "need orders, tile, kernel_variant and repeats >= 1");
+  if (op != IGASF_MASS && op != IGASF_STIFFNESS) return set_error(IGASF_ERR_INVALID_ARG, "bad op");
+  ApplyKernel cand[kMaxCandidates];
+  const int nc = list_apply_kernels(d, orders[0], prec, cand, kMaxCandidates);
+  if (nc < 1) return set_error(IGASF_ERR_UNSUPPORTED, "no kernel for this order and precision");
+  double best = 1e300;
+  int best_i = -1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  void *u = nullptr, *v = nullptr;
+  int rc = IGASF_OK;
+  for (int i = 0; i < nc && ce == cudaSuccess && rc == IGASF_OK; ++i) {
+    igasf_options o;
+    memset(&o, 0, sizeof(o));
+    o.precisions = IGASF_PREC_BIT(prec);
+    o.default_prec = prec;
+    for (int a = 0; a < d; ++a) o.tile[a] = cand[i].S[a];
+    o.kernel_variant = cand[i].variant;
+    igasf_handle h = nullptr;
+    rc = igasf_setup(d, orders, knot_lengths, knots, ctrl, coef, &o, &h);
+    if (rc != IGASF_OK) break;
+    const size_t bytes = (size_t)igasf_num_dofs(h) * (prec == IGASF_FP64 ? 8 : 4);
+    if (!u) {
+      ce = cudaMalloc(&u, bytes);
+      if (ce == cudaSuccess) ce = cudaMalloc(&v, bytes);
+      if (ce == cudaSuccess) ce = cudaMemset(u, 0, bytes);
+    }
+    for (int w = 0; w < 2 && ce == cudaSuccess && rc == IGASF_OK; ++w)
+      rc = igasf_apply_prec(h, op, prec, u, v, s);   // warm-up
+    if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+    for (int r = 0; r < repeats && ce == cudaSuccess && rc == IGASF_OK; ++r)
+      rc = igasf_apply_prec(h, op, prec, u, v, s);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    const int drc = igasf_destroy(h);
+    if (rc == IGASF_OK) rc = drc;
+    if (ce == cudaSuccess && rc == IGASF_OK && ms / repeats < best) {
+      best = ms / repeats;
+      best_i = i;
+    }
+  }
+  cudaFree(u);
+  cudaFree(v);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  if (rc != IGASF_OK) return rc;
+  if (ce != cudaSuccess) return set_error(IGASF_ERR_CUDA, (std::string("autotune: ") + cudaGetErrorString(ce)).c_str());
+  for (int a = 0; a < 3; ++a) tile[a] = a < d ? cand[best_i].S[a] : 1;
+  *kernel_variant = cand[best_i].variant;
+  if (best_ms) *best_ms = best;
+  return IGASF_OK;
+}

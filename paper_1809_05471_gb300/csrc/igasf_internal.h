@@ -34,6 +34,14 @@ struct ApplyParams {
   int skip_slab;              // test hook: tile 0 never fills this factor slab (-1: off)
 };
 
+// Many patches' tiles in one launch (device arrays): params[patch], and for
+// every block its patch and the patch's first block.
+struct BatchParams {
+  const ApplyParams *params;
+  const int *block_patch;
+  const int *first_block;
+};
+
 // A compiled apply kernel for one (d, p, precision) and its tile shape.
 struct ApplyKernel {
   int S[kMaxDim];             // elements per tile
@@ -43,6 +51,8 @@ struct ApplyKernel {
   int lanes;                  // pencils per thread (1, or 2 for packed FP32x2)
   int variant;                // IGASF_KERNEL_* (which factor-stream scheme)
   cudaError_t (*launch[2])(const ApplyParams &, cudaStream_t);
+  // batched launch over `blocks` tiles of several patches (nullptr if not built)
+  cudaError_t (*launch_batched[2])(const BatchParams &, int blocks, cudaStream_t);
   cudaError_t (*prepare)();   // raise the dynamic shared memory limit once
 };
 

@@ -38,6 +38,8 @@ EXPORTED = [
     "igasf_num_dofs", "igasf_num_quad_points", "igasf_describe", "igasf_get_tables",
     "igasf_get_factors", "igasf_profile_begin", "igasf_profile_end", "igasf_apply_noalloc",
     "igasf_device_status", "igasf_set_test_fault", "igasf_cg_solve",
+    "igasf_batch_create", "igasf_batch_apply", "igasf_batch_info", "igasf_batch_destroy",
+    "igasf_autotune",
     "igasf_last_error_message", "igasf_version",
 ]
 
@@ -103,6 +105,14 @@ def load_library(path: str = LIB_PATH):
     lib.igasf_apply_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     lib.igasf_cg_solve.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int, ctypes.POINTER(CgReport), vp]
+    lib.igasf_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(vp)]
+    lib.igasf_batch_apply.argtypes = [vp, vp, vp, vp]
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.igasf_batch_info.argtypes = [vp, i64p, i64p, i64p, ip]
+    lib.igasf_batch_destroy.argtypes = [vp]
+    lib.igasf_autotune.argtypes = [ctypes.c_int, ip, ip, ctypes.POINTER(dp), dp, ctypes.POINTER(Coef),
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip, dp]
     lib.igasf_device_status.argtypes = [vp, ctypes.c_int]
     lib.igasf_set_test_fault.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
     lib.igasf_profile_begin.argtypes = [vp, ctypes.c_int]
@@ -282,3 +292,61 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def autotune(patch, op: int = STIFFNESS, prec: int = FP32, repeats: int = 5):
+    """Fastest compiled (tile, kernel variant) for this patch, and its ms per apply."""
+    lib = load_library()
+    d = patch.d
+    knots = [np.ascontiguousarray(t, dtype=np.float64) for t in patch.knots]
+    dp = ctypes.POINTER(ctypes.c_double)
+    kptrs = (dp * d)(*[_dptr(t) for t in knots])
+    lens = (ctypes.c_int * d)(*[len(t) for t in knots])
+    orders = (ctypes.c_int * d)(*patch.orders)
+    ctrl = np.ascontiguousarray(patch.ctrl, dtype=np.float64).reshape(-1)
+    cv = None if patch.coef_values is None else np.ascontiguousarray(patch.coef_values, np.float64)
+    coef = Coef(patch.coef_kind, patch.coef_constant, patch.coef_alpha, _dptr(cv))
+    tile = (ctypes.c_int * 3)()
+    variant = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib.igasf_autotune(d, orders, lens, kptrs, _dptr(ctrl), ctypes.byref(coef), int(op),
+                              int(prec), int(repeats), tile, ctypes.byref(variant),
+                              ctypes.byref(ms)))
+    return list(tile), int(variant.value), float(ms.value)
+
+
+class Batch:
+    """igasf_batch over plans (which must outlive it): one graph launch per apply."""
+
+    def __init__(self, plans: Sequence[Plan], op: int = STIFFNESS, prec: int = FP32):
+        lib = load_library()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h().value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib.igasf_batch_create(len(self.plans), arr, int(op), int(prec), ctypes.byref(h)))
+        self.handle = h
+        self.offsets = np.cumsum([0] + [p.num_dofs for p in self.plans])
+        td, tq, fb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        ng = ctypes.c_int()
+        _check(lib.igasf_batch_info(h, ctypes.byref(td), ctypes.byref(tq), ctypes.byref(fb),
+                                    ctypes.byref(ng)))
+        self.total_dofs, self.total_quad_points = int(td.value), int(tq.value)
+        self.factor_bytes, self.launch_groups = int(fb.value), int(ng.value)
+
+    def apply(self, u, v, stream=None):
+        _check(load_library().igasf_batch_apply(self.handle, u.data_ptr(), v.data_ptr(),
+                                                _stream_handle(stream)))
+        return v
+
+    def close(self):
+        if self.handle is not None:
+            _check(load_library().igasf_batch_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+

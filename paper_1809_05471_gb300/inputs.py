@@ -166,3 +166,25 @@ def scaled_error(v: np.ndarray, v_ref: np.ndarray, a_inf: float, u: np.ndarray) 
     """Max-norm error scaled by ||A||_inf ||u||_inf."""
     den = a_inf * float(np.max(np.abs(u)))
     return float(np.max(np.abs(np.asarray(v, np.float64) - v_ref))) / den
+
+
+def config_batch(n: int = 256, seed: int = 7):
+    """Many independent d=3 patches: elements per direction uniform in 8..48
+    (each axis drawn separately), order uniform in 2..6, a constant coefficient
+    a ~ U[0.5, 2]. Geometry noise: 0.2 / (largest element count of the patch),
+    capped at a third of the patch's smallest Greville gap so that every map stays
+    a diffeomorphism. The per-patch parameters come from default_rng(seed); patch i
+    draws its noise and u from default_rng(1000 * seed + i)."""
+    rng = np.random.default_rng(seed)
+    Ks = rng.integers(8, 49, size=(n, 3))
+    ps = rng.integers(2, 7, size=n)
+    coefs = rng.uniform(0.5, 2.0, size=n)
+    out = []
+    for i in range(n):
+        p, K = int(ps[i]), [int(k) for k in Ks[i]]
+        gap = min(np.diff(greville(open_uniform_knots(p, k), p)).min() for k in K)
+        amp = min(0.2 / max(K), gap / 3.0)
+        out.append(make_patch(3, p, K, noise_amp=amp, seed=1000 * seed + i,
+                              coef_constant=float(coefs[i])))
+    return out
+

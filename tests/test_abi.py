@@ -148,6 +148,11 @@ def test_null_handle_calls(lib):
     assert lib.igasf_device_status(None, 0) == -1
     assert lib.igasf_set_test_fault(None, 0, 100000) == -1
     assert lib.igasf_cg_solve(None, 1, None, None, 1e-10, 1e-4, 10, None, None) == -1
+    assert lib.igasf_batch_create(0, None, 1, 1, None) == -1
+    assert lib.igasf_batch_apply(None, None, None, None) == -1
+    assert lib.igasf_batch_info(None, None, None, None, None) == -1
+    assert lib.igasf_batch_destroy(None) == 0
+    assert lib.igasf_autotune(3, None, None, None, None, None, 1, 1, 1, None, None, None) == -1
 
 
 def test_binding_raises_without_library(tmp_path):
