@@ -15,7 +15,9 @@
 // The factors stream through a ring of R slab buffers in shared memory, filled
 // by bulk copies (cp.async.bulk, the TMA engine) that one lane of a dedicated
 // producer warp issues from kernel entry on, so the factor stream overlaps the
-// staging and the first two sweeps and keeps R slabs per block in flight.
+// staging and the first two sweeps, with up to R slabs per block in flight. A
+// block may walk several tiles (the producer then runs ahead across tile
+// boundaries); the launch uses one block per tile.
 // Each slot has a "full" mbarrier (the copy's transaction count) and an
 // "empty" mbarrier (one arrival per consumer warp once it has read the slot).
 // Every wait is bounded in clock cycles; a wait that runs out sets the plan's
@@ -123,7 +125,8 @@ struct TileF2 {
 };
 
 template <int P, int S1, int S2, int S3, bool STIFF>
-__device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const int tile) {
+__device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const int first_tile,
+                                                 const int tile_stride, const int tile_end) {
   using G = TileF2<P, S1, S2, S3>;
   constexpr int E1 = G::E1, E2 = G::E2, E3 = G::E3;
   constexpr int Q1 = G::Q1, Q2 = G::Q2, Q3 = G::Q3;
@@ -148,12 +151,6 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
   float *us = reinterpret_cast<float *>(STIFF ? Y2 + G::Y / 2 : Y0 + G::Y / 2);
 
   const int tid = threadIdx.x;
-  const int t1 = tile % prm.T[0];
-  const int t2 = (tile / prm.T[0]) % prm.T[1];
-  const int t3 = tile / (prm.T[0] * prm.T[1]);
-  const int e01 = t1 * S1, e02 = t2 * S2, e03 = t3 * S3;
-  const int ke3 = min(S3, prm.K[2] - e03);
-  const int nslab = ke3 * P;
 
   if (tid == 0) {
     for (int r = 0; r < R; ++r) {
@@ -164,322 +161,341 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
   }
   __syncthreads();
 
-  // ---- producer warp: one lane streams the tile's factor slabs into the ring
+  // ---- producer warp: one lane streams the factor slabs of all of this block's
+  // tiles into the ring, in the order the consumers use them (slab counter g)
   if (tid >= NTC) {
     if (tid == NTC) {
-      const unsigned char *src = static_cast<const unsigned char *>(prm.D) + (size_t)tile * Q3 * SB;
       bool bad = false;
-      for (int s = 0; s < nslab; ++s) {
-        const int slot = s % R;
-        if (s >= R && !mbar_wait_bounded(smem_addr(&empty[slot]), ((s / R) - 1) & 1, prm.wait_limit))
-          bad = true;
-        if (tile == 0 && s == prm.skip_slab) continue;   // test hook: a fill that never comes
-        mbar_arrive_expect_tx(smem_addr(&full[slot]), SB);
-        bulk_copy_g2s(smem_addr(ring + (size_t)slot * SB), src + (size_t)s * SB, SB,
-                      smem_addr(&full[slot]));
+      uint32_t g = 0;
+      for (int tile = first_tile; tile < tile_end; tile += tile_stride) {
+        const int t3 = tile / (prm.T[0] * prm.T[1]);
+        const int nslab = min(S3, prm.K[2] - t3 * S3) * P;
+        const unsigned char *src = static_cast<const unsigned char *>(prm.D) + (size_t)tile * Q3 * SB;
+        for (int s = 0; s < nslab; ++s, ++g) {
+          const uint32_t slot = g % R;
+          if (g >= (uint32_t)R &&
+              !mbar_wait_bounded(smem_addr(&empty[slot]), ((g / R) - 1) & 1, prm.wait_limit))
+            bad = true;
+          if (tile == 0 && s == prm.skip_slab) continue;   // test hook: a fill that never comes
+          mbar_arrive_expect_tx(smem_addr(&full[slot]), SB);
+          bulk_copy_g2s(smem_addr(ring + (size_t)slot * SB), src + (size_t)s * SB, SB,
+                        smem_addr(&full[slot]));
+        }
       }
-      // leave no copy in flight: wait for the last fill of every slot
-      const int used = nslab < R ? nslab : R;
-      for (int slot = 0; slot < used; ++slot) {
-        const int last = (nslab - 1 - slot) / R;
-        if (!mbar_wait_bounded(smem_addr(&full[slot]), last & 1, prm.wait_limit)) bad = true;
+      // leave no copy in flight: wait for the last fill of every slot used
+      const uint32_t used = g < (uint32_t)R ? g : (uint32_t)R;
+      for (uint32_t k = 0; k < used; ++k) {
+        const uint32_t gi = g - 1 - k;
+        if (!mbar_wait_bounded(smem_addr(&full[gi % R]), (gi / R) & 1, prm.wait_limit)) bad = true;
       }
       if (bad) atomicOr(prm.status, 1u);
     }
     return;
   }
 
-  // ---- stage tables and the u tile (selection S_D u of eq. loc-basis-change)
-  {
-    const float *gb1 = static_cast<const float *>(prm.tabB[0]), *gd1 = static_cast<const float *>(prm.tabD[0]);
-    const float *gb2 = static_cast<const float *>(prm.tabB[1]), *gd2 = static_cast<const float *>(prm.tabD[1]);
-    const float *gb3 = static_cast<const float *>(prm.tabB[2]), *gd3 = static_cast<const float *>(prm.tabD[2]);
-    for (int i = tid; i < P * Q1; i += NTC) {
-      const int j = i / Q1, q = i - j * Q1;
-      t1b[i] = gb1[j * prm.Qpad[0] + e01 * P + q];
-      if (STIFF) t1d[i] = gd1[j * prm.Qpad[0] + e01 * P + q];
-    }
-    for (int i = tid; i < PP * Q2; i += NTC) {
-      const int q = i / PP, j = i - q * PP;
-      const float b = j < P ? gb2[j * prm.Qpad[1] + e02 * P + q] : 0.f;
-      t2b[2 * i] = b;
-      t2b[2 * i + 1] = b;
-      if (STIFF) {
-        const float db = j < P ? gd2[j * prm.Qpad[1] + e02 * P + q] : 0.f;
-        t2d[2 * i] = db;
-        t2d[2 * i + 1] = db;
-      }
-    }
-    for (int i = tid; i < PP * Q3; i += NTC) {
-      const int q = i / PP, j = i - q * PP;
-      const float b = j < P ? gb3[j * prm.Qpad[2] + e03 * P + q] : 0.f;
-      t3b[2 * i] = b;
-      t3b[2 * i + 1] = b;
-      if (STIFF) {
-        const float db = j < P ? gd3[j * prm.Qpad[2] + e03 * P + q] : 0.f;
-        t3d[2 * i] = db;
-        t3d[2 * i + 1] = db;
-      }
-    }
-    const float *u = static_cast<const float *>(prm.u);
-    const int N1 = prm.N[0], N2 = prm.N[1], N3 = prm.N[2];
-    for (int i = tid; i < G::VOL; i += NTC) {
-      const int n1 = i % E1, r = i / E1;
-      const int n2 = r % E2, n3 = r / E2;
-      const int g1 = e01 + n1, g2 = e02 + n2, g3 = e03 + n3;
-      float val = 0.f;
-      if (g1 < N1 && g2 < N2 && g3 < N3) val = u[((int64_t)g3 * N2 + g2) * N1 + g1];
-      us[i] = val;
-    }
-  }
-  consumer_sync(NTC);
+  uint32_t gbase = 0;   // slabs of earlier tiles of this block
+  for (int tile = first_tile; tile < tile_end; tile += tile_stride) {
+    const int t1 = tile % prm.T[0];
+    const int t2 = (tile / prm.T[0]) % prm.T[1];
+    const int t3 = tile / (prm.T[0] * prm.T[1]);
+    const int e01 = t1 * S1, e02 = t2 * S2, e03 = t3 * S3;
+    const int ke3 = min(S3, prm.K[2] - e03);
+    const int nslab = ke3 * P;
 
-  // ---- A: direction 1, X0 = B1 u, X1 = B1' u, one pencil pair per item
-  for (int i = tid; i < E3 * E2 * H1; i += NTC) {
-    const int k = i % H1, r = i / H1;
-    const int qa = 2 * k;
-    const int ea = qa / P, eb = (qa + 1) / P;
-    const float *ur = us + r * E1;
-    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const float2 uu = make_float2(ur[ea + j], ur[eb + j]);
-      a0 = ffma2(*reinterpret_cast<const float2 *>(t1b + j * Q1 + qa), uu, a0);
-      if (STIFF) a1 = ffma2(*reinterpret_cast<const float2 *>(t1d + j * Q1 + qa), uu, a1);
-    }
-    X0[r * XS + k] = a0;
-    if (STIFF) X1[r * XS + k] = a1;
-  }
-  consumer_sync(NTC);
-
-  // ---- B: direction 2, one (n3, element e2, pair) per item: p inputs -> p outputs
-  for (int i = tid; i < E3 * S2 * H1; i += NTC) {
-    const int k = i % H1, t = i / H1;
-    const int e2 = t % S2, n3 = t / S2;
-    float2 xa[P], xb[P];
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      xa[j] = X0[(n3 * E2 + e2 + j) * XS + k];
-      if (STIFF) xb[j] = X1[(n3 * E2 + e2 + j) * XS + k];
-    }
-#pragma unroll
-    for (int qq = 0; qq < P; ++qq) {
-      const int q2 = e2 * P + qq;
-      const float4 *b4 = reinterpret_cast<const float4 *>(t2b + q2 * 2 * PP);
-      const float4 *d4 = reinterpret_cast<const float4 *>(t2d + q2 * 2 * PP);
-      float2 y00 = make_float2(0.f, 0.f), y01 = y00, y10 = y00;
-#pragma unroll
-      for (int jj = 0; jj < PP / 2; ++jj) {
-        const float4 bb = b4[jj];
-        const int j0 = 2 * jj, j1 = 2 * jj + 1;
-        y00 = ffma2(make_float2(bb.x, bb.y), xa[j0], y00);
+    // ---- stage tables and the u tile (selection S_D u of eq. loc-basis-change)
+    {
+      const float *gb1 = static_cast<const float *>(prm.tabB[0]), *gd1 = static_cast<const float *>(prm.tabD[0]);
+      const float *gb2 = static_cast<const float *>(prm.tabB[1]), *gd2 = static_cast<const float *>(prm.tabD[1]);
+      const float *gb3 = static_cast<const float *>(prm.tabB[2]), *gd3 = static_cast<const float *>(prm.tabD[2]);
+      for (int i = tid; i < P * Q1; i += NTC) {
+        const int j = i / Q1, q = i - j * Q1;
+        t1b[i] = gb1[j * prm.Qpad[0] + e01 * P + q];
+        if (STIFF) t1d[i] = gd1[j * prm.Qpad[0] + e01 * P + q];
+      }
+      for (int i = tid; i < PP * Q2; i += NTC) {
+        const int q = i / PP, j = i - q * PP;
+        const float b = j < P ? gb2[j * prm.Qpad[1] + e02 * P + q] : 0.f;
+        t2b[2 * i] = b;
+        t2b[2 * i + 1] = b;
         if (STIFF) {
-          const float4 dd = d4[jj];
-          y01 = ffma2(make_float2(dd.x, dd.y), xa[j0], y01);
-          y10 = ffma2(make_float2(bb.x, bb.y), xb[j0], y10);
-          if (j1 < P) {
-            y01 = ffma2(make_float2(dd.z, dd.w), xa[j1], y01);
-            y10 = ffma2(make_float2(bb.z, bb.w), xb[j1], y10);
-          }
+          const float db = j < P ? gd2[j * prm.Qpad[1] + e02 * P + q] : 0.f;
+          t2d[2 * i] = db;
+          t2d[2 * i + 1] = db;
         }
-        if (j1 < P) y00 = ffma2(make_float2(bb.z, bb.w), xa[j1], y00);
       }
-      const int idx = n3 * YS + q2 * H1 + k;
-      Y0[idx] = y00;
-      if (STIFF) {
-        Y1[idx] = y01;
-        Y2[idx] = y10;
+      for (int i = tid; i < PP * Q3; i += NTC) {
+        const int q = i / PP, j = i - q * PP;
+        const float b = j < P ? gb3[j * prm.Qpad[2] + e03 * P + q] : 0.f;
+        t3b[2 * i] = b;
+        t3b[2 * i + 1] = b;
+        if (STIFF) {
+          const float db = j < P ? gd3[j * prm.Qpad[2] + e03 * P + q] : 0.f;
+          t3d[2 * i] = db;
+          t3d[2 * i + 1] = db;
+        }
+      }
+      const float *u = static_cast<const float *>(prm.u);
+      const int N1 = prm.N[0], N2 = prm.N[1], N3 = prm.N[2];
+      for (int i = tid; i < G::VOL; i += NTC) {
+        const int n1 = i % E1, r = i / E1;
+        const int n2 = r % E2, n3 = r / E2;
+        const int g1 = e01 + n1, g2 = e02 + n2, g3 = e03 + n3;
+        float val = 0.f;
+        if (g1 < N1 && g2 < N2 && g3 < N3) val = u[((int64_t)g3 * N2 + g2) * N1 + g1];
+        us[i] = val;
       }
     }
-  }
-  consumer_sync(NTC);
+    consumer_sync(NTC);
 
-  // ---- C: pencil pairs: direction-3 sweep, product with D, transposed sweep
-  {
-    const bool has_pair = tid < NPAIR;
-    const int lane = tid & 31;
-    bool bad = false;
-    float2 y0[E3], y1[E3], y2[E3], z0[E3], z1[E3], z2[E3];
-#pragma unroll
-    for (int n = 0; n < E3; ++n) {
-      const float2 zero = make_float2(0.f, 0.f);
-      y0[n] = has_pair ? Y0[n * YS + tid] : zero;
-      z0[n] = zero;
-      if (STIFF) {
-        y1[n] = has_pair ? Y1[n * YS + tid] : zero;
-        y2[n] = has_pair ? Y2[n * YS + tid] : zero;
-        z1[n] = zero;
-        z2[n] = zero;
+    // ---- A: direction 1, X0 = B1 u, X1 = B1' u, one pencil pair per item
+    for (int i = tid; i < E3 * E2 * H1; i += NTC) {
+      const int k = i % H1, r = i / H1;
+      const int qa = 2 * k;
+      const int ea = qa / P, eb = (qa + 1) / P;
+      const float *ur = us + r * E1;
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+  #pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const float2 uu = make_float2(ur[ea + j], ur[eb + j]);
+        a0 = ffma2(*reinterpret_cast<const float2 *>(t1b + j * Q1 + qa), uu, a0);
+        if (STIFF) a1 = ffma2(*reinterpret_cast<const float2 *>(t1d + j * Q1 + qa), uu, a1);
       }
+      X0[r * XS + k] = a0;
+      if (STIFF) X1[r * XS + k] = a1;
     }
-#pragma unroll
-    for (int e3 = 0; e3 < S3; ++e3) {
-      if (e3 < ke3) {
-#pragma unroll
-        for (int qq = 0; qq < P; ++qq) {
-          const int q3 = e3 * P + qq;
-          const int slot = q3 % R, parity = (q3 / R) & 1;   // compile-time after unrolling
-          if (!mbar_wait_bounded(smem_addr(&full[slot]), parity, prm.wait_limit)) bad = true;
-          float4 dc[NCH];
-          float2 dm = make_float2(0.f, 0.f);
-          if (has_pair) {
-            if (STIFF) {
-              const float4 *rs = reinterpret_cast<const float4 *>(ring + (size_t)slot * SB);
-#pragma unroll
-              for (int c = 0; c < NCH; ++c) dc[c] = rs[c * UNITS + tid];
-            } else {
-              dm = reinterpret_cast<const float2 *>(ring + (size_t)slot * SB)[tid];
+    consumer_sync(NTC);
+
+    // ---- B: direction 2, one (n3, element e2, pair) per item: p inputs -> p outputs
+    for (int i = tid; i < E3 * S2 * H1; i += NTC) {
+      const int k = i % H1, t = i / H1;
+      const int e2 = t % S2, n3 = t / S2;
+      float2 xa[P], xb[P];
+  #pragma unroll
+      for (int j = 0; j < P; ++j) {
+        xa[j] = X0[(n3 * E2 + e2 + j) * XS + k];
+        if (STIFF) xb[j] = X1[(n3 * E2 + e2 + j) * XS + k];
+      }
+  #pragma unroll
+      for (int qq = 0; qq < P; ++qq) {
+        const int q2 = e2 * P + qq;
+        const float4 *b4 = reinterpret_cast<const float4 *>(t2b + q2 * 2 * PP);
+        const float4 *d4 = reinterpret_cast<const float4 *>(t2d + q2 * 2 * PP);
+        float2 y00 = make_float2(0.f, 0.f), y01 = y00, y10 = y00;
+  #pragma unroll
+        for (int jj = 0; jj < PP / 2; ++jj) {
+          const float4 bb = b4[jj];
+          const int j0 = 2 * jj, j1 = 2 * jj + 1;
+          y00 = ffma2(make_float2(bb.x, bb.y), xa[j0], y00);
+          if (STIFF) {
+            const float4 dd = d4[jj];
+            y01 = ffma2(make_float2(dd.x, dd.y), xa[j0], y01);
+            y10 = ffma2(make_float2(bb.x, bb.y), xb[j0], y10);
+            if (j1 < P) {
+              y01 = ffma2(make_float2(dd.z, dd.w), xa[j1], y01);
+              y10 = ffma2(make_float2(bb.z, bb.w), xb[j1], y10);
             }
           }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(smem_addr(&empty[slot]));
-          if (!has_pair) continue;
-          float2 b[PP], db[PP];
-          {
-            const float4 *b4 = reinterpret_cast<const float4 *>(t3b + q3 * 2 * PP);
-            const float4 *d4 = reinterpret_cast<const float4 *>(t3d + q3 * 2 * PP);
-#pragma unroll
-            for (int jj = 0; jj < PP / 2; ++jj) {
-              const float4 bb = b4[jj];
-              b[2 * jj] = make_float2(bb.x, bb.y);
-              b[2 * jj + 1] = make_float2(bb.z, bb.w);
+          if (j1 < P) y00 = ffma2(make_float2(bb.z, bb.w), xa[j1], y00);
+        }
+        const int idx = n3 * YS + q2 * H1 + k;
+        Y0[idx] = y00;
+        if (STIFF) {
+          Y1[idx] = y01;
+          Y2[idx] = y10;
+        }
+      }
+    }
+    consumer_sync(NTC);
+
+    // ---- C: pencil pairs: direction-3 sweep, product with D, transposed sweep
+    {
+      const bool has_pair = tid < NPAIR;
+      const int lane = tid & 31;
+      bool bad = false;
+      float2 y0[E3], y1[E3], y2[E3], z0[E3], z1[E3], z2[E3];
+  #pragma unroll
+      for (int n = 0; n < E3; ++n) {
+        const float2 zero = make_float2(0.f, 0.f);
+        y0[n] = has_pair ? Y0[n * YS + tid] : zero;
+        z0[n] = zero;
+        if (STIFF) {
+          y1[n] = has_pair ? Y1[n * YS + tid] : zero;
+          y2[n] = has_pair ? Y2[n * YS + tid] : zero;
+          z1[n] = zero;
+          z2[n] = zero;
+        }
+      }
+  #pragma unroll
+      for (int e3 = 0; e3 < S3; ++e3) {
+        if (e3 < ke3) {
+  #pragma unroll
+          for (int qq = 0; qq < P; ++qq) {
+            const int q3 = e3 * P + qq;
+            const uint32_t g = gbase + q3, slot = g % R, parity = (g / R) & 1;
+            if (!mbar_wait_bounded(smem_addr(&full[slot]), parity, prm.wait_limit)) bad = true;
+            float4 dc[NCH];
+            float2 dm = make_float2(0.f, 0.f);
+            if (has_pair) {
               if (STIFF) {
-                const float4 dd = d4[jj];
-                db[2 * jj] = make_float2(dd.x, dd.y);
-                db[2 * jj + 1] = make_float2(dd.z, dd.w);
+                const float4 *rs = reinterpret_cast<const float4 *>(ring + (size_t)slot * SB);
+  #pragma unroll
+                for (int c = 0; c < NCH; ++c) dc[c] = rs[c * UNITS + tid];
+              } else {
+                dm = reinterpret_cast<const float2 *>(ring + (size_t)slot * SB)[tid];
+              }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&empty[slot]));
+            if (!has_pair) continue;
+            float2 b[PP], db[PP];
+            {
+              const float4 *b4 = reinterpret_cast<const float4 *>(t3b + q3 * 2 * PP);
+              const float4 *d4 = reinterpret_cast<const float4 *>(t3d + q3 * 2 * PP);
+  #pragma unroll
+              for (int jj = 0; jj < PP / 2; ++jj) {
+                const float4 bb = b4[jj];
+                b[2 * jj] = make_float2(bb.x, bb.y);
+                b[2 * jj + 1] = make_float2(bb.z, bb.w);
+                if (STIFF) {
+                  const float4 dd = d4[jj];
+                  db[2 * jj] = make_float2(dd.x, dd.y);
+                  db[2 * jj + 1] = make_float2(dd.z, dd.w);
+                }
+              }
+            }
+            if (STIFF) {
+              float2 d1 = make_float2(0.f, 0.f), d2 = d1, d3 = d1;
+  #pragma unroll
+              for (int j = 0; j < P; ++j) {
+                d3 = ffma2(db[j], y0[e3 + j], d3);
+                d2 = ffma2(b[j], y1[e3 + j], d2);
+                d1 = ffma2(b[j], y2[e3 + j], d1);
+              }
+              const float2 D11 = make_float2(dc[0].x, dc[0].y), D12 = make_float2(dc[0].z, dc[0].w);
+              const float2 D13 = make_float2(dc[1].x, dc[1].y), D22 = make_float2(dc[1].z, dc[1].w);
+              const float2 D23 = make_float2(dc[2].x, dc[2].y), D33 = make_float2(dc[2].z, dc[2].w);
+              const float2 g1 = ffma2(D13, d3, ffma2(D12, d2, fmul2(D11, d1)));
+              const float2 g2 = ffma2(D23, d3, ffma2(D22, d2, fmul2(D12, d1)));
+              const float2 g3 = ffma2(D33, d3, ffma2(D23, d2, fmul2(D13, d1)));
+  #pragma unroll
+              for (int j = 0; j < P; ++j) {
+                z0[e3 + j] = ffma2(db[j], g3, z0[e3 + j]);   // W3
+                z1[e3 + j] = ffma2(b[j], g2, z1[e3 + j]);    // W2
+                z2[e3 + j] = ffma2(b[j], g1, z2[e3 + j]);    // W1
+              }
+            } else {
+              float2 uq = make_float2(0.f, 0.f);
+  #pragma unroll
+              for (int j = 0; j < P; ++j) uq = ffma2(b[j], y0[e3 + j], uq);
+              const float2 w = fmul2(dm, uq);
+  #pragma unroll
+              for (int j = 0; j < P; ++j) z0[e3 + j] = ffma2(b[j], w, z0[e3 + j]);
+            }
+          }
+        }
+      }
+      if (has_pair) {
+  #pragma unroll
+        for (int n = 0; n < E3; ++n) {
+          Y0[n * YS + tid] = z0[n];
+          if (STIFF) {
+            Y1[n * YS + tid] = z1[n];
+            Y2[n * YS + tid] = z2[n];
+          }
+        }
+      }
+      if (bad) atomicOr(prm.status, 1u);
+    }
+    consumer_sync(NTC);
+
+    // ---- D: transposed direction 2, register-blocked over all q2 of the tile
+    for (int i = tid; i < E3 * H1; i += NTC) {
+      const int k = i % H1, n3 = i / H1;
+      float2 ya[E2], yb[E2];
+  #pragma unroll
+      for (int n = 0; n < E2; ++n) {
+        ya[n] = make_float2(0.f, 0.f);
+        yb[n] = ya[n];
+      }
+  #pragma unroll
+      for (int q2 = 0; q2 < Q2; ++q2) {
+        const int e2 = q2 / P;
+        const int idx = n3 * YS + q2 * H1 + k;
+        const float2 w3 = Y0[idx];
+        float2 w2 = make_float2(0.f, 0.f), w1 = w2;
+        if (STIFF) {
+          w2 = Y1[idx];
+          w1 = Y2[idx];
+        }
+        const float4 *b4 = reinterpret_cast<const float4 *>(t2b + q2 * 2 * PP);
+        const float4 *d4 = reinterpret_cast<const float4 *>(t2d + q2 * 2 * PP);
+  #pragma unroll
+        for (int jj = 0; jj < PP / 2; ++jj) {
+          const float4 bb = b4[jj];
+          const float4 dd = STIFF ? d4[jj] : bb;
+  #pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = 2 * jj + h;
+            if (j < P) {
+              const float2 bj = h ? make_float2(bb.z, bb.w) : make_float2(bb.x, bb.y);
+              ya[e2 + j] = ffma2(bj, w3, ya[e2 + j]);
+              if (STIFF) {
+                const float2 dj = h ? make_float2(dd.z, dd.w) : make_float2(dd.x, dd.y);
+                ya[e2 + j] = ffma2(dj, w2, ya[e2 + j]);
+                yb[e2 + j] = ffma2(bj, w1, yb[e2 + j]);
               }
             }
           }
-          if (STIFF) {
-            float2 d1 = make_float2(0.f, 0.f), d2 = d1, d3 = d1;
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-              d3 = ffma2(db[j], y0[e3 + j], d3);
-              d2 = ffma2(b[j], y1[e3 + j], d2);
-              d1 = ffma2(b[j], y2[e3 + j], d1);
-            }
-            const float2 D11 = make_float2(dc[0].x, dc[0].y), D12 = make_float2(dc[0].z, dc[0].w);
-            const float2 D13 = make_float2(dc[1].x, dc[1].y), D22 = make_float2(dc[1].z, dc[1].w);
-            const float2 D23 = make_float2(dc[2].x, dc[2].y), D33 = make_float2(dc[2].z, dc[2].w);
-            const float2 g1 = ffma2(D13, d3, ffma2(D12, d2, fmul2(D11, d1)));
-            const float2 g2 = ffma2(D23, d3, ffma2(D22, d2, fmul2(D12, d1)));
-            const float2 g3 = ffma2(D33, d3, ffma2(D23, d2, fmul2(D13, d1)));
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-              z0[e3 + j] = ffma2(db[j], g3, z0[e3 + j]);   // W3
-              z1[e3 + j] = ffma2(b[j], g2, z1[e3 + j]);    // W2
-              z2[e3 + j] = ffma2(b[j], g1, z2[e3 + j]);    // W1
-            }
+        }
+      }
+  #pragma unroll
+      for (int n = 0; n < E2; ++n) {
+        X0[(n3 * E2 + n) * XS + k] = ya[n];
+        if (STIFF) X1[(n3 * E2 + n) * XS + k] = yb[n];
+      }
+    }
+    consumer_sync(NTC);
+
+    // ---- E: transposed direction 1, one (n3, n2) row per item, all q1 in registers
+    float *vp = static_cast<float *>(prm.vpart) + (size_t)tile * G::VOL;
+    for (int r = tid; r < E3 * E2; r += NTC) {
+      float2 acc[E1];
+  #pragma unroll
+      for (int n = 0; n < E1; ++n) acc[n] = make_float2(0.f, 0.f);
+  #pragma unroll
+      for (int k = 0; k < H1; ++k) {
+        const int qa = 2 * k, ea = qa / P, eb = (qa + 1) / P;
+        const float2 ya = X0[r * XS + k];
+        const float2 yb = STIFF ? X1[r * XS + k] : make_float2(0.f, 0.f);
+  #pragma unroll
+        for (int j = 0; j < P; ++j) {
+          const float2 bt = *reinterpret_cast<const float2 *>(t1b + j * Q1 + qa);
+          const float2 dt = STIFF ? *reinterpret_cast<const float2 *>(t1d + j * Q1 + qa) : bt;
+          if (ea == eb) {
+            acc[ea + j] = ffma2(bt, ya, acc[ea + j]);
+            if (STIFF) acc[ea + j] = ffma2(dt, yb, acc[ea + j]);
           } else {
-            float2 uq = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int j = 0; j < P; ++j) uq = ffma2(b[j], y0[e3 + j], uq);
-            const float2 w = fmul2(dm, uq);
-#pragma unroll
-            for (int j = 0; j < P; ++j) z0[e3 + j] = ffma2(b[j], w, z0[e3 + j]);
-          }
-        }
-      }
-    }
-    if (has_pair) {
-#pragma unroll
-      for (int n = 0; n < E3; ++n) {
-        Y0[n * YS + tid] = z0[n];
-        if (STIFF) {
-          Y1[n * YS + tid] = z1[n];
-          Y2[n * YS + tid] = z2[n];
-        }
-      }
-    }
-    if (bad) atomicOr(prm.status, 1u);
-  }
-  consumer_sync(NTC);
-
-  // ---- D: transposed direction 2, register-blocked over all q2 of the tile
-  for (int i = tid; i < E3 * H1; i += NTC) {
-    const int k = i % H1, n3 = i / H1;
-    float2 ya[E2], yb[E2];
-#pragma unroll
-    for (int n = 0; n < E2; ++n) {
-      ya[n] = make_float2(0.f, 0.f);
-      yb[n] = ya[n];
-    }
-#pragma unroll
-    for (int q2 = 0; q2 < Q2; ++q2) {
-      const int e2 = q2 / P;
-      const int idx = n3 * YS + q2 * H1 + k;
-      const float2 w3 = Y0[idx];
-      float2 w2 = make_float2(0.f, 0.f), w1 = w2;
-      if (STIFF) {
-        w2 = Y1[idx];
-        w1 = Y2[idx];
-      }
-      const float4 *b4 = reinterpret_cast<const float4 *>(t2b + q2 * 2 * PP);
-      const float4 *d4 = reinterpret_cast<const float4 *>(t2d + q2 * 2 * PP);
-#pragma unroll
-      for (int jj = 0; jj < PP / 2; ++jj) {
-        const float4 bb = b4[jj];
-        const float4 dd = STIFF ? d4[jj] : bb;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int j = 2 * jj + h;
-          if (j < P) {
-            const float2 bj = h ? make_float2(bb.z, bb.w) : make_float2(bb.x, bb.y);
-            ya[e2 + j] = ffma2(bj, w3, ya[e2 + j]);
+            acc[ea + j].x = fmaf(bt.x, ya.x, acc[ea + j].x);
+            acc[eb + j].y = fmaf(bt.y, ya.y, acc[eb + j].y);
             if (STIFF) {
-              const float2 dj = h ? make_float2(dd.z, dd.w) : make_float2(dd.x, dd.y);
-              ya[e2 + j] = ffma2(dj, w2, ya[e2 + j]);
-              yb[e2 + j] = ffma2(bj, w1, yb[e2 + j]);
+              acc[ea + j].x = fmaf(dt.x, yb.x, acc[ea + j].x);
+              acc[eb + j].y = fmaf(dt.y, yb.y, acc[eb + j].y);
             }
           }
         }
       }
+  #pragma unroll
+      for (int n = 0; n < E1; ++n) vp[r * E1 + n] = acc[n].x + acc[n].y;
     }
-#pragma unroll
-    for (int n = 0; n < E2; ++n) {
-      X0[(n3 * E2 + n) * XS + k] = ya[n];
-      if (STIFF) X1[(n3 * E2 + n) * XS + k] = yb[n];
-    }
-  }
-  consumer_sync(NTC);
-
-  // ---- E: transposed direction 1, one (n3, n2) row per item, all q1 in registers
-  float *vp = static_cast<float *>(prm.vpart) + (size_t)tile * G::VOL;
-  for (int r = tid; r < E3 * E2; r += NTC) {
-    float2 acc[E1];
-#pragma unroll
-    for (int n = 0; n < E1; ++n) acc[n] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < H1; ++k) {
-      const int qa = 2 * k, ea = qa / P, eb = (qa + 1) / P;
-      const float2 ya = X0[r * XS + k];
-      const float2 yb = STIFF ? X1[r * XS + k] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        const float2 bt = *reinterpret_cast<const float2 *>(t1b + j * Q1 + qa);
-        const float2 dt = STIFF ? *reinterpret_cast<const float2 *>(t1d + j * Q1 + qa) : bt;
-        if (ea == eb) {
-          acc[ea + j] = ffma2(bt, ya, acc[ea + j]);
-          if (STIFF) acc[ea + j] = ffma2(dt, yb, acc[ea + j]);
-        } else {
-          acc[ea + j].x = fmaf(bt.x, ya.x, acc[ea + j].x);
-          acc[eb + j].y = fmaf(bt.y, ya.y, acc[eb + j].y);
-          if (STIFF) {
-            acc[ea + j].x = fmaf(dt.x, yb.x, acc[ea + j].x);
-            acc[eb + j].y = fmaf(dt.y, yb.y, acc[eb + j].y);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int n = 0; n < E1; ++n) vp[r * E1 + n] = acc[n].x + acc[n].y;
+    gbase += nslab;
+    consumer_sync(NTC);   // the next tile's staging overwrites what phase E reads
   }
 }
 
 template <int P, int S1, int S2, int S3, bool STIFF>
 __global__ void __launch_bounds__(TileF2<P, S1, S2, S3>::NT)
 apply3d_f32_kernel(const ApplyParams prm) {
-  apply3d_f32_body<P, S1, S2, S3, STIFF>(prm, blockIdx.x);
+  apply3d_f32_body<P, S1, S2, S3, STIFF>(prm, blockIdx.x, gridDim.x, prm.ntiles);
 }
 
 // Many patches in one launch: block b works on tile b - first_block[patch] of
@@ -488,9 +504,12 @@ template <int P, int S1, int S2, int S3, bool STIFF>
 __global__ void __launch_bounds__(TileF2<P, S1, S2, S3>::NT)
 apply3d_f32_batched(const BatchParams bp) {
   const int patch = bp.block_patch[blockIdx.x];
-  apply3d_f32_body<P, S1, S2, S3, STIFF>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
+  const int tile = blockIdx.x - bp.first_block[patch];
+  apply3d_f32_body<P, S1, S2, S3, STIFF>(bp.params[patch], tile, 1, tile + 1);
 }
 
+// One block per tile (a persistent grid that walks tiles with a stride was
+// measured slower on this workload; the body supports both).
 template <int P, int S1, int S2, int S3, bool STIFF>
 cudaError_t launch_apply3d_f32(const ApplyParams &prm, cudaStream_t s) {
   using G = TileF2<P, S1, S2, S3>;

@@ -1,8 +1,8 @@
 // 3D apply kernels of order p = 3. FP64: scalar kernel, tile 8, 4, 4 elements.
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload):
-//   register prefetch, tile 8, 4, 4
 //   TMA ring, tile 8, 8, 4
+//   register prefetch, tile 8, 4, 4
 //   register prefetch, tile 4, 4, 4
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
 #include "apply3d.cuh"
@@ -18,10 +18,11 @@ int apply3d_p3(int prec, ApplyKernel *out, int max_out) {
     return n;
   }
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = make_apply3d_f32r<3, 8, 4, 4>();
   if (n < max_out) out[n++] = make_apply3d_f32<3, 8, 8, 4>();
+  if (n < max_out) out[n++] = make_apply3d_f32r<3, 8, 4, 4>();
   if (n < max_out) out[n++] = make_apply3d_f32r<3, 4, 4, 4>();
 #else
+  if (n < max_out) out[n++] = make_apply3d_f32<3, 8, 8, 4>();
   if (n < max_out) out[n++] = make_apply3d_f32r<3, 8, 4, 4>();
   if (n < max_out) out[n++] = make_apply3d_f32r<3, 4, 4, 4>();
   if (n < max_out) out[n++] = make_apply3d_f32r<3, 8, 8, 4>();
@@ -30,7 +31,6 @@ int apply3d_p3(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = make_apply3d_f32r<3, 8, 4, 2>();
   if (n < max_out) out[n++] = make_apply3d_f32<3, 8, 4, 4>();
   if (n < max_out) out[n++] = make_apply3d_f32<3, 4, 4, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32<3, 8, 8, 4>();
   if (n < max_out) out[n++] = make_apply3d_f32<3, 8, 8, 2>();
   if (n < max_out) out[n++] = make_apply3d_f32<3, 4, 4, 2>();
   if (n < max_out) out[n++] = make_apply3d_f32<3, 8, 4, 2>();

@@ -1,9 +1,9 @@
 // 3D apply kernels of order p = 6. FP64: scalar kernel, tile 4, 2, 2 elements.
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload):
+//   register prefetch, tile 2, 2, 2
 //   register prefetch, tile 4, 4, 2
 //   TMA ring, tile 4, 2, 2
-//   register prefetch, tile 2, 2, 4
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
@@ -18,14 +18,14 @@ int apply3d_p6(int prec, ApplyKernel *out, int max_out) {
     return n;
   }
 #ifndef IGASF_TILE_SEARCH
+  if (n < max_out) out[n++] = make_apply3d_f32r<6, 2, 2, 2>();
   if (n < max_out) out[n++] = make_apply3d_f32r<6, 4, 4, 2>();
   if (n < max_out) out[n++] = make_apply3d_f32<6, 4, 2, 2>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<6, 2, 2, 4>();
 #else
+  if (n < max_out) out[n++] = make_apply3d_f32r<6, 2, 2, 2>();
   if (n < max_out) out[n++] = make_apply3d_f32r<6, 4, 4, 2>();
   if (n < max_out) out[n++] = make_apply3d_f32r<6, 2, 2, 4>();
   if (n < max_out) out[n++] = make_apply3d_f32r<6, 4, 2, 2>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<6, 2, 2, 2>();
   if (n < max_out) out[n++] = make_apply3d_f32r<6, 4, 4, 1>();
   if (n < max_out) out[n++] = make_apply3d_f32<6, 4, 4, 2>();
   if (n < max_out) out[n++] = make_apply3d_f32<6, 2, 2, 4>();
