@@ -62,6 +62,9 @@ def _load():
                                                     _dp, ctypes.c_int]
         lib.orc_apply_elementwise.argtypes = patch_args + [ctypes.c_int, _dp, _dp]
         lib.orc_max_threads.argtypes = []
+        lib.orc_round_significand.argtypes = [ctypes.c_double, ctypes.c_int]
+        lib.orc_round_significand.restype = ctypes.c_double
+        lib.orc_set_stored_factor_bits.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -199,6 +202,31 @@ def apply_elementwise(patch, op: int, u):
 
 def max_threads() -> int:
     return int(_load().orc_max_threads())
+
+
+BF16_BITS = 8   # significant bits of bfloat16
+
+
+def round_significand(x: float, bits: int) -> float:
+    """x rounded to `bits` significant bits, ties to even (the oracle's rule for
+    factors stored in a narrower format)."""
+    return float(_load().orc_round_significand(float(x), int(bits)))
+
+
+class stored_factor_bits:
+    """Within the block, every oracle operator uses weighted factors w F rounded
+    to `bits` significant bits (8: bfloat16 storage); 0 restores FP64."""
+
+    def __init__(self, bits: int):
+        self.bits = int(bits)
+
+    def __enter__(self):
+        _check(_load().orc_set_stored_factor_bits(self.bits))
+        return self
+
+    def __exit__(self, *exc):
+        _check(_load().orc_set_stored_factor_bits(0))
+        return False
 
 
 class use_library:

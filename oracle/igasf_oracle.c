@@ -355,9 +355,52 @@ static double basis_at(const orc_patch *P, const int *q, const int *n, int deriv
   return r;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Stored factors in a narrower format                                       */
+/* ------------------------------------------------------------------------ */
+
+/* A matrix-free apply stores the weighted factors w F at every quadrature
+ * point (Sec. 6.2) and may store them in a narrower floating-point format than
+ * FP64. The operator it applies is then the quadrature operator whose factors
+ * are the rounded values. With stored_bits > 0 the oracle computes exactly that
+ * operator: each stored product (w |det J| for the mass, each entry of
+ * w a |det J| J^-1 J^-T for the stiffness) is rounded to stored_bits
+ * significant bits, ties to even, before it enters the sums. 8 bits is the
+ * significand of bfloat16; the exponent range is not limited (the factors lie
+ * far inside bfloat16's range). 0 (the default) keeps every factor in FP64. */
+static int stored_bits = 0;
+
+/* x rounded to `bits` significant bits, ties to even (x = m 2^e with
+ * 1/2 <= |m| < 1, so m 2^bits lies in [2^(bits-1), 2^bits) and rounding it to
+ * an integer keeps `bits` significant bits). */
+double orc_round_significand(double x, int bits) {
+  if (bits <= 0 || bits >= 53 || x == 0.0 || !isfinite(x)) return x;
+  int e;
+  double m = frexp(x, &e);
+  return ldexp(nearbyint(ldexp(m, bits)), e - bits);
+}
+
+int orc_set_stored_factor_bits(int bits) {
+  if (bits < 0 || bits > 53) return ORC_ERR_ARG;
+  stored_bits = bits;
+  return ORC_OK;
+}
+
 /* integrand of A_mn at one quadrature point: w F d^theta phi_n d^eta phi_m */
 static double integrand(const orc_patch *P, const orc_qp *g, const int *q, const int *m,
                         const int *n, int op) {
+  if (stored_bits > 0) {
+    if (op == ORC_MASS)
+      return orc_round_significand(g->w * g->FM, stored_bits) * basis_at(P, q, m, -1) *
+             basis_at(P, q, n, -1);
+    double s = 0.0;
+    for (int i = 0; i < P->d; ++i) {
+      double dm = basis_at(P, q, m, i);
+      for (int j = 0; j < P->d; ++j)
+        s += dm * orc_round_significand(g->w * g->FK[i][j], stored_bits) * basis_at(P, q, n, j);
+    }
+    return s;
+  }
   if (op == ORC_MASS) return g->w * g->FM * basis_at(P, q, m, -1) * basis_at(P, q, n, -1);
   double s = 0.0;
   for (int i = 0; i < P->d; ++i) {

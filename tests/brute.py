@@ -39,8 +39,11 @@ def tables(t, p):
     return x, w, np.nan_to_num(B), np.nan_to_num(dB)
 
 
-def dense_operator(patch, op):
-    """Dense A (N x N) for op 0 = mass, 1 = stiffness."""
+def dense_operator(patch, op, round_factor=None):
+    """Dense A (N x N) for op 0 = mass, 1 = stiffness. If given,
+    ``round_factor`` maps each array of weighted factors w F (w |det J|, or one
+    entry (i, j) of w a |det J| J^-1 J^-T) to the values actually stored."""
+    rf = round_factor if round_factor is not None else (lambda x: x)
     d = patch.d
     tabs = [tables(t, p) for t, p in zip(patch.knots, patch.orders)]
     Ns = [tb[2].shape[1] for tb in tabs]
@@ -69,12 +72,12 @@ def dense_operator(patch, op):
     else:
         a = np.full(len(w), patch.coef_constant)
     if op == 0:
-        return Phi.T @ ((w * np.abs(det))[:, None] * Phi)
+        return Phi.T @ (rf(w * np.abs(det))[:, None] * Phi)
     F = (a * np.abs(det))[:, None, None] * np.einsum("qik,qjk->qij", Jinv, Jinv)
     A = np.zeros((Phi.shape[1], Phi.shape[1]))
     for i in range(d):
         for j in range(d):
-            A += dPhi[i].T @ ((w * F[:, i, j])[:, None] * dPhi[j])
+            A += dPhi[i].T @ (rf(w * F[:, i, j])[:, None] * dPhi[j])
     return A
 
 

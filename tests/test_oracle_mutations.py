@@ -32,6 +32,15 @@ MUTATIONS = [
      "s += dm * g->FK[i][j] * basis_at(P, q, n, i);"),
     ("transposed operand in J", "out->J[i][j] += c * dphi;", "out->J[j][i] += c * dphi;"),
     ("row support window", "ehi[a] = m[a] + P.p[a] - 1;", "ehi[a] = m[a] + P.p[a] - 2;"),
+    ("stored stiffness factor rounded before the weight",
+     "orc_round_significand(g->w * g->FK[i][j], stored_bits)",
+     "g->w * orc_round_significand(g->FK[i][j], stored_bits)"),
+    ("stored mass factor rounded before the weight",
+     "orc_round_significand(g->w * g->FM, stored_bits)",
+     "g->w * orc_round_significand(g->FM, stored_bits)"),
+    ("rounding halves away from zero", "nearbyint(ldexp(m, bits))", "round(ldexp(m, bits))"),
+    ("one significant bit too many", "return ldexp(nearbyint(ldexp(m, bits)), e - bits);",
+     "return ldexp(nearbyint(ldexp(m, bits + 1)), e - bits - 1);"),
 ]
 
 
@@ -61,6 +70,18 @@ def _quick_pins():
         vr, _ = O.apply_rows(patch, op, u, rows)
         if not np.max(np.abs(vr - Ab @ u)) < 1e-13 * np.max(np.abs(Ab @ u)):
             failed.append("rows op %d" % op)
+    # bfloat16-stored factors: ties to even, and the rounded quantity is w F
+    if not (O.round_significand(1 + 2.0 ** -8, 8) == 1.0
+            and O.round_significand(1 + 3 * 2.0 ** -8, 8) == 1 + 2.0 ** -6
+            and O.round_significand(1 + 2.0 ** -7, 8) == 1 + 2.0 ** -7):
+        failed.append("bf16 rounding")
+    for op in (O.MASS, O.STIFFNESS):
+        with O.stored_factor_bits(O.BF16_BITS):
+            A = O.csr_to_dense(*O.assemble_csr(patch, op), patch.num_dofs)
+        Ab = brute.dense_operator(patch, op, round_factor=lambda x: np.ldexp(
+            np.round(np.frexp(x)[0] * 256.0), np.frexp(x)[1] - 8))
+        if not np.max(np.abs(A - Ab)) < 1e-13 * np.max(np.abs(Ab)):
+            failed.append("bf16 brute-force op %d" % op)
     return failed
 
 

@@ -353,3 +353,70 @@ def test_quad_data_coefficient_at_physical_point():
     a = np.exp(0.5 * np.sin(2 * np.pi * G[:, 0]) * np.cos(2 * np.pi * G[:, 1]))
     assert np.max(np.abs(qd["a"] - a)) < 1e-15
     assert np.all(qd["detJ"] > 0)
+
+
+# --- factors stored in a narrower format (bfloat16) ---------------------------
+
+def _bf16_numpy(x):
+    """Round to 8 significant bits, ties to even, with numpy (frexp, and
+    np.round, which rounds halves to even)."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.round(m * 256.0), e - 8)
+
+
+def test_round_significand_matches_torch_bfloat16():
+    """The oracle's rounding to 8 significant bits is bfloat16's round to
+    nearest even: compared with torch's float32 -> bfloat16 conversion on
+    float32 values (exact in float64, so there is no double rounding), ties
+    included."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    x32 = (rng.standard_normal(4000) * np.exp2(rng.integers(-60, 60, 4000))).astype(np.float32)
+    bits = x32.view(np.uint32)
+    ties = (bits[:500] & np.uint32(0xFFFF0000)) | np.uint32(0x8000)   # exact halfway cases
+    x32 = np.concatenate([x32, ties.view(np.float32)])
+    ref = torch.from_numpy(x32.copy()).to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([O.round_significand(float(v), O.BF16_BITS) for v in x32.astype(np.float64)])
+    assert np.array_equal(got, ref)
+
+
+def test_round_significand_24_bits_is_float32():
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(2000) * np.exp2(rng.integers(-100, 100, 2000))
+    got = np.array([O.round_significand(float(v), 24) for v in x])
+    assert np.array_equal(got, x.astype(np.float32).astype(np.float64))
+    assert O.round_significand(0.0, 8) == 0.0
+
+
+@pytest.mark.parametrize("d,p,K,op", [(2, 3, 2, 0), (2, 4, 2, 1), (3, 2, 2, 1), (3, 3, 2, 0),
+                                      (3, 3, 2, 1)])
+def test_bf16_stored_factors_match_brute_force(d, p, K, op):
+    """With stored_factor_bits(8) the oracle's operator is the quadrature
+    operator whose weighted factors w F are rounded to bfloat16: the numpy
+    brute force with the same rounding applied to w |det J| and to each
+    w a |det J| (J^-1 J^-T)_ij agrees, and both differ from the FP64 operator
+    by about the bfloat16 rounding."""
+    patch, _ = I.make_patch(d, p, K, noise_amp=0.1, seed=21,
+                            coef_kind=I.COEF_EXP_SIN_COS, coef_alpha=0.5)
+    N = patch.num_dofs
+    with O.stored_factor_bits(O.BF16_BITS):
+        A = O.csr_to_dense(*O.assemble_csr(patch, op), N)
+    A64 = O.csr_to_dense(*O.assemble_csr(patch, op), N)
+    Ab = brute.dense_operator(patch, op, round_factor=_bf16_numpy)
+    s = np.max(np.abs(Ab))
+    assert np.max(np.abs(A - Ab)) < 1e-13 * s
+    rel = np.max(np.abs(A - A64)) / s
+    assert 1e-5 < rel < 2.0 ** -7
+
+
+def test_bf16_stored_mass_sums_to_rounded_weights():
+    """1^T M 1 with bfloat16-stored factors is the sum over quadrature points of
+    the rounded w |det J| (the rounded quantity is the weighted factor, not
+    |det J| alone)."""
+    patch, _ = I.config_cube(p=3, K=3)
+    qd = O.quad_data(patch)
+    with O.stored_factor_bits(O.BF16_BITS):
+        rp, ci, va = O.assemble_csr(patch, O.MASS)
+    expect = np.sum(_bf16_numpy(qd["w"] * qd["FM"]))
+    assert abs(va.sum() - expect) < 1e-14 * expect
+    assert abs(va.sum() - 1.0) > 1e-6     # no longer the exact volume
