@@ -61,10 +61,17 @@ typedef enum {
 
 typedef enum { IGASF_MASS = 0, IGASF_STIFFNESS = 1 } igasf_op;
 
-/* Arithmetic of an apply. FP64: FP64 factors, tables and vectors.
- * FP32: FP32 factors, tables, vectors and arithmetic (factors are computed in
- * FP64 at setup and rounded once). */
-typedef enum { IGASF_FP64 = 0, IGASF_FP32 = 1 } igasf_prec;
+/* Arithmetic of an apply. The factors w F are always computed in FP64 at
+ * setup (Sec. 6.2); a precision says how they are stored and how the apply
+ * computes.
+ * FP64: FP64 factors, tables, vectors and arithmetic.
+ * FP32: FP32 factors (each rounded once), tables, vectors and arithmetic.
+ * BF16: factors stored in bfloat16 (each rounded once to nearest even, half
+ *       the bytes of FP32); tables, vectors (u, v: float) and arithmetic FP32.
+ *       The operator applied is the quadrature operator with those rounded
+ *       factors: about 2^-9 relative perturbation of every w F, meant for
+ *       inner solves and preconditioners. */
+typedef enum { IGASF_FP64 = 0, IGASF_FP32 = 1, IGASF_BF16 = 2 } igasf_prec;
 #define IGASF_PREC_BIT(prec) (1u << (unsigned)(prec))
 
 /* Coefficient a of the stiffness operator (Example 1 with A = a I, evaluated
@@ -93,8 +100,8 @@ typedef struct {
   int reserved[7];       /* must be zero */
 } igasf_options;
 
-/* How the FP32 3D tile kernel receives its factors (FP64 and 2D kernels have
- * one scheme: per-thread loads). */
+/* How the FP32 and BF16 3D tile kernels receive their factors (FP64 and 2D
+ * kernels have one scheme: per-thread loads). */
 enum {
   IGASF_KERNEL_DEFAULT = 0,
   IGASF_KERNEL_REGISTERS = 1, /* each thread loads its factors into registers, slabs ahead */
@@ -145,7 +152,7 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
 /*
  * v = A u on `stream` in the handle's default precision (Alg. 2 after Alg. 3,
  * localized per Sec. 4). u and v: device arrays of num_dofs values of the
- * precision's type (double for FP64, float for FP32), aligned to that type,
+ * precision's type (double for FP64, float for FP32 and BF16), aligned to it,
  * not overlapping. v is overwritten. Asynchronous: returns after enqueueing; it
  * allocates nothing and does not synchronise. Errors: INVALID_ARG (null or
  * misaligned pointer, bad op), UNSUPPORTED (precision not stored at setup),
@@ -207,7 +214,7 @@ int igasf_profile_end(igasf_handle h, double *ms, int *applies);
 
 /*
  * Device status of the plan. Kernels that wait on shared-memory barriers (the
- * FP32 3D tile kernel, whose factor stream arrives by bulk copies) bound every
+ * FP32/BF16 3D tile kernels whose factor stream arrives by bulk copies) bound every
  * wait by a clock-cycle limit; a wait that runs out sets a status word on the
  * device and the kernel finishes without hanging, but its result is invalid.
  * This call waits for the device, then returns IGASF_ERR_TIMEOUT if the word is
@@ -216,7 +223,7 @@ int igasf_profile_end(igasf_handle h, double *ms, int *applies);
 int igasf_device_status(igasf_handle h, int clear);
 
 /*
- * Test hook for the bounded waits: from now on, tile 0 of every FP32 3D apply
+ * Test hook for the bounded waits: from now on, tile 0 of every FP32/BF16 3D apply
  * on this handle never receives factor slab `skip_slab` (-1 turns this off),
  * and every wait gives up after `wait_limit_cycles` clock cycles (default 2e9,
  * about one second; minimum 1000). Results of applies made while a slab is
@@ -268,12 +275,16 @@ typedef struct {
  *     r = b - K x with the FP64 apply; inner PCG on K d = r with the FP32 apply,
  *     FP32 vectors and FP64 dot products, to ||r_inner|| <= inner_rtol ||r||;
  *     x += d. Stops when the FP64 residual satisfies ||r|| <= rtol ||b||.
+ *   inner_prec = IGASF_BF16: the same refinement with the BF16 apply inside
+ *     (factors in bfloat16: the inner operator differs from K by about 2^-9
+ *     relative, which the FP64 outer residual corrects; more outer steps,
+ *     cheaper inner iterations).
  * The Jacobi diagonal of K is computed on the device in FP64 at the first call
  * and kept in the plan.
  *
  * b, x: device arrays of num_dofs doubles (boundary entries of b are ignored);
  * x is overwritten (the solve starts from zero). The plan must store FP64 (and
- * FP32 for the refined solve). max_iterations bounds the total inner
+ * inner_prec for the refined solve). max_iterations bounds the total inner
  * iterations. Synchronous; allocates its vectors for the duration of the call.
  * report may be NULL. Errors: INVALID_ARG, UNSUPPORTED (d != 3 or a missing
  * precision), CUDA, OOM. Not converging is not an error: see report->converged.

@@ -1,11 +1,14 @@
-// 2D apply kernels for p = 2..9 (FP64 and FP32); tile = 8 x 8 elements.
+// 2D apply kernels for p = 2..9 (FP64, FP32, and FP32 with bfloat16-stored
+// factors); tile = 8 x 8 elements.
 #include "apply2d.cuh"
 
 namespace igasf {
 
 template <int P>
 static ApplyKernel get2(int prec) {
-  return prec == IGASF_FP64 ? make_apply2d<double, P, 8, 8>() : make_apply2d<float, P, 8, 8>();
+  if (prec == IGASF_FP64) return make_apply2d<double, P, 8, 8>();
+  if (prec == IGASF_FP32) return make_apply2d<float, P, 8, 8>();
+  return make_apply2d<float, P, 8, 8, __nv_bfloat16>();
 }
 
 ApplyKernel apply2d_any(int p, int prec) {

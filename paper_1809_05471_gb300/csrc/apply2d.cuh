@@ -9,11 +9,20 @@
 //   g = D grad u (3 stored entries)
 //   W2 = B2'^T g2, W1 = B2^T g1           registers -> shared
 //   v = B1^T W2 + B1'^T W1                -> per-tile partial v
+// T is the arithmetic type (double or float), TF the stored factor type (T,
+// or bfloat16 with float arithmetic).
 #pragma once
+
+#include <cuda_bf16.h>
 
 #include "igasf_internal.h"
 
 namespace igasf {
+
+template <typename T>
+__device__ __forceinline__ T load_factor(const T *p) { return __ldcs(p); }
+template <typename T>
+__device__ __forceinline__ T load_factor(const __nv_bfloat16 *p) { return (T)__bfloat162float(__ldcs(p)); }
 
 template <int P, int S1, int S2>
 struct Tile2 {
@@ -28,7 +37,7 @@ struct Tile2 {
   static constexpr size_t smem_words(bool stiff) { return 2 * TAB + VOL + (stiff ? 2 : 1) * X; }
 };
 
-template <typename T, int P, int S1, int S2, bool STIFF>
+template <typename T, typename TF, int P, int S1, int S2, bool STIFF>
 __global__ void __launch_bounds__(Tile2<P, S1, S2>::NT)
 apply2d_kernel(const ApplyParams prm) {
   using G = Tile2<P, S1, S2>;
@@ -87,7 +96,7 @@ apply2d_kernel(const ApplyParams prm) {
     const int q1 = tid;
     const bool valid = (e01 + q1 / P < prm.K[0]);
     const int ke2 = min(S2, prm.K[1] - e02);
-    const T *Dt = static_cast<const T *>(prm.D) + (size_t)tile * Q2 * NF * PL + tid;
+    const TF *Dt = static_cast<const TF *>(prm.D) + (size_t)tile * Q2 * NF * PL + tid;
     T y0[E2], y1[E2], z0[E2], z1[E2];
 #pragma unroll
     for (int n = 0; n < E2; ++n) {
@@ -104,13 +113,13 @@ apply2d_kernel(const ApplyParams prm) {
 #pragma unroll
         for (int qq = 0; qq < P; ++qq) {
           const int q2 = e2 * P + qq;
-          const T *Dq = Dt + (size_t)q2 * NF * PL;
+          const TF *Dq = Dt + (size_t)q2 * NF * PL;
           if (STIFF) {
             T D11 = T(0), D12 = T(0), D22 = T(0);
             if (valid) {
-              D11 = __ldcs(Dq);
-              D12 = __ldcs(Dq + PL);
-              D22 = __ldcs(Dq + 2 * PL);
+              D11 = load_factor<T>(Dq);
+              D12 = load_factor<T>(Dq + PL);
+              D22 = load_factor<T>(Dq + 2 * PL);
             }
             T d1 = T(0), d2 = T(0);
 #pragma unroll
@@ -126,7 +135,7 @@ apply2d_kernel(const ApplyParams prm) {
               z1[e2 + j] = fma(tb2[j * Q2 + q2], g1, z1[e2 + j]);  // W1 (goes with B1'^T)
             }
           } else {
-            const T Dm = valid ? __ldcs(Dq) : T(0);
+            const T Dm = valid ? load_factor<T>(Dq) : T(0);
             T uq = T(0);
 #pragma unroll
             for (int j = 0; j < P; ++j) uq = fma(tb2[j * Q2 + q2], y0[e2 + j], uq);
@@ -165,26 +174,26 @@ apply2d_kernel(const ApplyParams prm) {
   }
 }
 
-template <typename T, int P, int S1, int S2, bool STIFF>
+template <typename T, typename TF, int P, int S1, int S2, bool STIFF>
 cudaError_t launch_apply2d(const ApplyParams &prm, cudaStream_t s) {
   using G = Tile2<P, S1, S2>;
-  apply2d_kernel<T, P, S1, S2, STIFF><<<prm.ntiles, G::NT, G::smem_words(STIFF) * sizeof(T), s>>>(prm);
+  apply2d_kernel<T, TF, P, S1, S2, STIFF><<<prm.ntiles, G::NT, G::smem_words(STIFF) * sizeof(T), s>>>(prm);
   return cudaGetLastError();
 }
 
-template <typename T, int P, int S1, int S2>
+template <typename T, typename TF, int P, int S1, int S2>
 cudaError_t prepare_apply2d() {
   using G = Tile2<P, S1, S2>;
-  cudaError_t e = cudaFuncSetAttribute(apply2d_kernel<T, P, S1, S2, false>,
+  cudaError_t e = cudaFuncSetAttribute(apply2d_kernel<T, TF, P, S1, S2, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(G::smem_words(false) * sizeof(T)));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(apply2d_kernel<T, P, S1, S2, true>,
+  return cudaFuncSetAttribute(apply2d_kernel<T, TF, P, S1, S2, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(G::smem_words(true) * sizeof(T)));
 }
 
-template <typename T, int P, int S1, int S2>
+template <typename T, int P, int S1, int S2, typename TF = T>
 ApplyKernel make_apply2d() {
   using G = Tile2<P, S1, S2>;
   static_assert(G::NT <= 1024, "tile too large for one block");
@@ -198,11 +207,11 @@ ApplyKernel make_apply2d() {
   k.plane = G::PL;
   k.lanes = 1;
   k.variant = IGASF_KERNEL_REGISTERS;
-  k.launch[IGASF_MASS] = &launch_apply2d<T, P, S1, S2, false>;
-  k.launch[IGASF_STIFFNESS] = &launch_apply2d<T, P, S1, S2, true>;
+  k.launch[IGASF_MASS] = &launch_apply2d<T, TF, P, S1, S2, false>;
+  k.launch[IGASF_STIFFNESS] = &launch_apply2d<T, TF, P, S1, S2, true>;
   k.launch_batched[IGASF_MASS] = nullptr;
   k.launch_batched[IGASF_STIFFNESS] = nullptr;
-  k.prepare = &prepare_apply2d<T, P, S1, S2>;
+  k.prepare = &prepare_apply2d<T, TF, P, S1, S2>;
   return k;
 }
 

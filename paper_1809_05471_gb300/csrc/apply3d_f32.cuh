@@ -27,6 +27,8 @@
 // 128-bit load feeds two FFMA2 table operands; the X and Y arrays have padded
 // row strides so the register-blocked sweeps read shared memory without bank
 // conflicts.
+// BF (template flag): the factors are stored in bfloat16 (half the slab
+// bytes) and widened to FP32 when read; everything else is unchanged.
 #pragma once
 
 #include "igasf_internal.h"
@@ -36,6 +38,28 @@ namespace igasf {
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// ---- stored factor chunks of one pencil pair (layout.h: [chunk][unit][CE]) ----
+// FP32: a float4 holds two fields of both pencils (stiffness, three chunks), a
+// float2 the one mass field of both pencils. bfloat16: the same values in half
+// the bytes (uint2, one 32-bit word); each 32-bit word is one field of the two
+// pencils, and widening is exact (bfloat16 is the high half of an FP32 word).
+template <bool STIFF, bool BF> struct FactorChunk;
+template <> struct FactorChunk<true, false> { using type = float4; };
+template <> struct FactorChunk<false, false> { using type = float2; };
+template <> struct FactorChunk<true, true> { using type = uint2; };
+template <> struct FactorChunk<false, true> { using type = uint32_t; };
+
+__device__ __forceinline__ float2 bf16x2_to_float2(uint32_t w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+__device__ __forceinline__ float4 widen(float4 c) { return c; }
+__device__ __forceinline__ float2 widen(float2 c) { return c; }
+__device__ __forceinline__ float4 widen(uint2 c) {
+  const float2 a = bf16x2_to_float2(c.x), b = bf16x2_to_float2(c.y);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float2 widen(uint32_t c) { return bf16x2_to_float2(c); }
 
 // ---- mbarrier and bulk-copy helpers (shared-memory addresses as 32-bit) ----
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -111,20 +135,25 @@ struct TileF2 {
   static constexpr int VOL = E1 * E2 * E3;
   static constexpr int X = 2 * E3 * E2 * XS;        // floats per X array
   static constexpr int Y = 2 * E3 * YS;             // floats per Y array
-  // factor slab bytes and ring depth (about 48 KB of slabs in flight per block)
-  __host__ __device__ static constexpr uint32_t slab_bytes(bool stiff) { return stiff ? 3u * UNITS * 16u : UNITS * 8u; }
-  __host__ __device__ static constexpr int ring(bool stiff) {
-    return (int)(49152u / slab_bytes(stiff)) < 2 ? 2
-           : ((int)(49152u / slab_bytes(stiff)) > Q3 ? Q3 : (int)(49152u / slab_bytes(stiff)));
+  // factor slab bytes (bf: bfloat16 factors) and ring depth (about 48 KB of
+  // slabs in flight per block)
+  __host__ __device__ static constexpr uint32_t slab_bytes(bool stiff, bool bf) {
+    return (stiff ? 3u * UNITS * 16u : UNITS * 8u) / (bf ? 2u : 1u);
   }
-  __host__ __device__ static constexpr size_t ring_bytes(bool stiff) { return (size_t)ring(stiff) * slab_bytes(stiff); }
-  __host__ __device__ static constexpr size_t smem_bytes(bool stiff) {
-    return ring_bytes(stiff) + 16 * (size_t)ring(stiff) +
+  __host__ __device__ static constexpr int ring(bool stiff, bool bf) {
+    return (int)(49152u / slab_bytes(stiff, bf)) < 2 ? 2
+           : ((int)(49152u / slab_bytes(stiff, bf)) > Q3 ? Q3 : (int)(49152u / slab_bytes(stiff, bf)));
+  }
+  __host__ __device__ static constexpr size_t ring_bytes(bool stiff, bool bf) {
+    return (size_t)ring(stiff, bf) * slab_bytes(stiff, bf);
+  }
+  __host__ __device__ static constexpr size_t smem_bytes(bool stiff, bool bf) {
+    return ring_bytes(stiff, bf) + 16 * (size_t)ring(stiff, bf) +
            4 * ((size_t)T2 + T3 + T1 + (stiff ? 2 : 1) * X + (stiff ? 3 : 1) * Y + VOL);
   }
 };
 
-template <int P, int S1, int S2, int S3, bool STIFF>
+template <int P, int S1, int S2, int S3, bool STIFF, bool BF>
 __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const int first_tile,
                                                  const int tile_stride, const int tile_end) {
   using G = TileF2<P, S1, S2, S3>;
@@ -132,13 +161,15 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
   constexpr int Q1 = G::Q1, Q2 = G::Q2, Q3 = G::Q3;
   constexpr int H1 = G::H1, PP = G::PP, NTC = G::NTC, NPAIR = G::NPAIR, UNITS = G::UNITS;
   constexpr int XS = G::XS, YS = G::YS;
-  constexpr int R = G::ring(STIFF);
-  constexpr uint32_t SB = G::slab_bytes(STIFF);
-  constexpr int NCH = STIFF ? 3 : 1;   // 16-byte chunks (stiffness) or one 8-byte chunk (mass)
+  constexpr int R = G::ring(STIFF, BF);
+  constexpr uint32_t SB = G::slab_bytes(STIFF, BF);
+  constexpr int NCH = STIFF ? 3 : 1;   // chunks of a pencil pair per slab
+  using Chunk = typename FactorChunk<STIFF, BF>::type;
+  static_assert(SB == NCH * UNITS * sizeof(Chunk), "slab size");
 
   extern __shared__ __align__(128) unsigned char smem_f32[];
   unsigned char *ring = smem_f32;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem_f32 + G::ring_bytes(STIFF));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_f32 + G::ring_bytes(STIFF, BF));
   uint64_t *empty = full + R;
   float *sm = reinterpret_cast<float *>(empty + R);
   float *t2b = sm, *t2d = t2b + 2 * PP * Q2;        // [q2][PP] float2 {b, b}
@@ -336,12 +367,12 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
             float4 dc[NCH];
             float2 dm = make_float2(0.f, 0.f);
             if (has_pair) {
-              if (STIFF) {
-                const float4 *rs = reinterpret_cast<const float4 *>(ring + (size_t)slot * SB);
+              const Chunk *rs = reinterpret_cast<const Chunk *>(ring + (size_t)slot * SB);
+              if constexpr (STIFF) {
   #pragma unroll
-                for (int c = 0; c < NCH; ++c) dc[c] = rs[c * UNITS + tid];
+                for (int c = 0; c < NCH; ++c) dc[c] = widen(rs[c * UNITS + tid]);
               } else {
-                dm = reinterpret_cast<const float2 *>(ring + (size_t)slot * SB)[tid];
+                dm = widen(rs[tid]);
               }
             }
             __syncwarp();
@@ -492,71 +523,72 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
   }
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF>
+template <int P, int S1, int S2, int S3, bool STIFF, bool BF>
 __global__ void __launch_bounds__(TileF2<P, S1, S2, S3>::NT)
 apply3d_f32_kernel(const ApplyParams prm) {
-  apply3d_f32_body<P, S1, S2, S3, STIFF>(prm, blockIdx.x, gridDim.x, prm.ntiles);
+  apply3d_f32_body<P, S1, S2, S3, STIFF, BF>(prm, blockIdx.x, gridDim.x, prm.ntiles);
 }
 
 // Many patches in one launch: block b works on tile b - first_block[patch] of
 // patch = block_patch[b], with that patch's parameters.
-template <int P, int S1, int S2, int S3, bool STIFF>
+template <int P, int S1, int S2, int S3, bool STIFF, bool BF>
 __global__ void __launch_bounds__(TileF2<P, S1, S2, S3>::NT)
 apply3d_f32_batched(const BatchParams bp) {
   const int patch = bp.block_patch[blockIdx.x];
   const int tile = blockIdx.x - bp.first_block[patch];
-  apply3d_f32_body<P, S1, S2, S3, STIFF>(bp.params[patch], tile, 1, tile + 1);
+  apply3d_f32_body<P, S1, S2, S3, STIFF, BF>(bp.params[patch], tile, 1, tile + 1);
 }
 
 // One block per tile (a persistent grid that walks tiles with a stride was
 // measured slower on this workload; the body supports both).
-template <int P, int S1, int S2, int S3, bool STIFF>
+template <int P, int S1, int S2, int S3, bool STIFF, bool BF>
 cudaError_t launch_apply3d_f32(const ApplyParams &prm, cudaStream_t s) {
   using G = TileF2<P, S1, S2, S3>;
-  apply3d_f32_kernel<P, S1, S2, S3, STIFF><<<prm.ntiles, G::NT, G::smem_bytes(STIFF), s>>>(prm);
+  apply3d_f32_kernel<P, S1, S2, S3, STIFF, BF><<<prm.ntiles, G::NT, G::smem_bytes(STIFF, BF), s>>>(prm);
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF>
+template <int P, int S1, int S2, int S3, bool STIFF, bool BF>
 cudaError_t launch_apply3d_f32_batched(const BatchParams &bp, int blocks, cudaStream_t s) {
   using G = TileF2<P, S1, S2, S3>;
-  apply3d_f32_batched<P, S1, S2, S3, STIFF><<<blocks, G::NT, G::smem_bytes(STIFF), s>>>(bp);
+  apply3d_f32_batched<P, S1, S2, S3, STIFF, BF><<<blocks, G::NT, G::smem_bytes(STIFF, BF), s>>>(bp);
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3>
+template <int P, int S1, int S2, int S3, bool BF>
 cudaError_t prepare_apply3d_f32() {
   using G = TileF2<P, S1, S2, S3>;
-  const int sm = (int)G::smem_bytes(false), sk = (int)G::smem_bytes(true);
+  const int sm = (int)G::smem_bytes(false, BF), sk = (int)G::smem_bytes(true, BF);
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, false>, a, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, true>, a, sk);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_batched<P, S1, S2, S3, false>, a, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_batched<P, S1, S2, S3, true>, a, sk);
+  cudaError_t e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, false, BF>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, true, BF>, a, sk);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_batched<P, S1, S2, S3, false, BF>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_batched<P, S1, S2, S3, true, BF>, a, sk);
   return e;
 }
 
-template <int P, int S1, int S2, int S3>
+// BF = true: the same kernel reading bfloat16-stored factors.
+template <int P, int S1, int S2, int S3, bool BF = false>
 ApplyKernel make_apply3d_f32() {
   using G = TileF2<P, S1, S2, S3>;
   static_assert(G::NT <= 1024, "tile too large for one block");
-  static_assert(G::smem_bytes(true) <= 227 * 1024, "tile exceeds shared memory");
-  static_assert(G::slab_bytes(false) % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static_assert(G::smem_bytes(true, BF) <= 227 * 1024, "tile exceeds shared memory");
+  static_assert(G::slab_bytes(false, BF) % 16 == 0, "bulk copies move multiples of 16 bytes");
   ApplyKernel k;
   k.S[0] = S1;
   k.S[1] = S2;
   k.S[2] = S3;
   k.threads = G::NT;
-  k.smem[IGASF_MASS] = G::smem_bytes(false);
-  k.smem[IGASF_STIFFNESS] = G::smem_bytes(true);
+  k.smem[IGASF_MASS] = G::smem_bytes(false, BF);
+  k.smem[IGASF_STIFFNESS] = G::smem_bytes(true, BF);
   k.plane = G::PL;
   k.lanes = 2;
   k.variant = IGASF_KERNEL_RING;
-  k.launch[IGASF_MASS] = &launch_apply3d_f32<P, S1, S2, S3, false>;
-  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32<P, S1, S2, S3, true>;
-  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32_batched<P, S1, S2, S3, false>;
-  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32_batched<P, S1, S2, S3, true>;
-  k.prepare = &prepare_apply3d_f32<P, S1, S2, S3>;
+  k.launch[IGASF_MASS] = &launch_apply3d_f32<P, S1, S2, S3, false, BF>;
+  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32<P, S1, S2, S3, true, BF>;
+  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32_batched<P, S1, S2, S3, false, BF>;
+  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32_batched<P, S1, S2, S3, true, BF>;
+  k.prepare = &prepare_apply3d_f32<P, S1, S2, S3, BF>;
   return k;
 }
 

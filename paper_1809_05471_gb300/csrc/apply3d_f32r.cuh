@@ -23,6 +23,9 @@
 // phase C every slab's loads are issued PD slabs ahead of their use.
 // Tables of directions 2 and 3 are held in shared memory as duplicated pairs
 // {b, b} so that one 128-bit load feeds two FFMA2 table operands.
+// BF (template flag): the factors are stored in bfloat16, so each prefetched
+// slab takes half the bytes and half the registers; they are widened to FP32
+// at use.
 #pragma once
 
 #include "apply3d_f32.cuh"
@@ -32,7 +35,8 @@
 namespace igasf {
 
 
-__device__ __forceinline__ float4 ldg_stream4(const float4 *p) {
+// Streaming (evict-first) loads of one factor chunk.
+__device__ __forceinline__ float4 ldg_stream(const float4 *p) {
   float4 r;
   asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];"
                : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
@@ -40,9 +44,21 @@ __device__ __forceinline__ float4 ldg_stream4(const float4 *p) {
   return r;
 }
 
-__device__ __forceinline__ float2 ldg_stream2(const float2 *p) {
+__device__ __forceinline__ float2 ldg_stream(const float2 *p) {
   float2 r;
   asm volatile("ld.global.cs.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
+  return r;
+}
+
+__device__ __forceinline__ uint2 ldg_stream(const uint2 *p) {
+  uint2 r;
+  asm volatile("ld.global.cs.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t ldg_stream(const uint32_t *p) {
+  uint32_t r;
+  asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(r) : "l"(p));
   return r;
 }
 
@@ -69,13 +85,14 @@ struct TileF2R {
   }
 };
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
 __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const int tile) {
   using G = TileF2R<P, S1, S2, S3>;
   constexpr int E1 = G::E1, E2 = G::E2, E3 = G::E3;
   constexpr int Q1 = G::Q1, Q2 = G::Q2, Q3 = G::Q3;
   constexpr int H1 = G::H1, PP = G::PP, NT = G::NT, NPAIR = G::NPAIR, UNITS = G::UNITS;
-  constexpr int NCH = STIFF ? 3 : 1;   // 16-byte chunks (stiffness) or one 8-byte chunk (mass)
+  constexpr int NCH = STIFF ? 3 : 1;   // chunks of a pencil pair per slab
+  using Chunk = typename FactorChunk<STIFF, BF>::type;
 
   extern __shared__ __align__(16) unsigned char smem_f32r[];
   float *sm = reinterpret_cast<float *>(smem_f32r);
@@ -98,19 +115,13 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
 
   // ---- request the first PD slabs of factors now (consumed in phase C)
   const bool has_pair = tid < NPAIR;
-  float4 dq4[PD][NCH];
-  float2 dq2[PD];
-  const float4 *D4 = reinterpret_cast<const float4 *>(prm.D) + (size_t)tile * Q3 * NCH * UNITS + tid;
-  const float2 *D2 = reinterpret_cast<const float2 *>(prm.D) + (size_t)tile * Q3 * UNITS + tid;
+  Chunk dq[PD][NCH];
+  const Chunk *Dc = reinterpret_cast<const Chunk *>(prm.D) + (size_t)tile * Q3 * NCH * UNITS + tid;
 #pragma unroll
   for (int s = 0; s < PD; ++s) {
     if (has_pair && s < nslab) {
-      if (STIFF) {
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) dq4[s][c] = ldg_stream4(D4 + ((size_t)s * NCH + c) * UNITS);
-      } else {
-        dq2[s] = ldg_stream2(D2 + (size_t)s * UNITS);
-      }
+      for (int c = 0; c < NCH; ++c) dq[s][c] = ldg_stream(Dc + ((size_t)s * NCH + c) * UNITS);
     }
   }
 
@@ -242,20 +253,16 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
           // factors of this slab, then request slab q3 + PD into the freed slot
           float4 dc[NCH];
           float2 dm = make_float2(0.f, 0.f);
-          if (STIFF) {
+          if constexpr (STIFF) {
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) dc[c] = dq4[q3 % PD][c];
+            for (int c = 0; c < NCH; ++c) dc[c] = widen(dq[q3 % PD][c]);
           } else {
-            dm = dq2[q3 % PD];
+            dm = widen(dq[q3 % PD][0]);
           }
           if (q3 + PD < nslab) {
-            if (STIFF) {
 #pragma unroll
-              for (int c = 0; c < NCH; ++c)
-                dq4[q3 % PD][c] = ldg_stream4(D4 + ((size_t)(q3 + PD) * NCH + c) * UNITS);
-            } else {
-              dq2[q3 % PD] = ldg_stream2(D2 + (size_t)(q3 + PD) * UNITS);
-            }
+            for (int c = 0; c < NCH; ++c)
+              dq[q3 % PD][c] = ldg_stream(Dc + ((size_t)(q3 + PD) * NCH + c) * UNITS);
           }
           float2 b[PP], db[PP];
           {
@@ -396,51 +403,52 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
   }
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
 apply3d_f32r_kernel(const ApplyParams prm) {
-  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD>(prm, blockIdx.x);
+  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(prm, blockIdx.x);
 }
 
 // Many patches in one launch: block b works on tile b - first_block[patch] of
 // patch = block_patch[b], with that patch's parameters.
-template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
 apply3d_f32r_batched(const BatchParams bp) {
   const int patch = bp.block_patch[blockIdx.x];
-  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
+  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
 cudaError_t launch_apply3d_f32r(const ApplyParams &prm, cudaStream_t s) {
   using G = TileF2R<P, S1, S2, S3>;
-  apply3d_f32r_kernel<P, S1, S2, S3, STIFF, PD>
+  apply3d_f32r_kernel<P, S1, S2, S3, STIFF, PD, BF>
       <<<prm.ntiles, G::NT, G::smem_floats(STIFF) * sizeof(float), s>>>(prm);
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
 cudaError_t launch_apply3d_f32r_batched(const BatchParams &bp, int blocks, cudaStream_t s) {
   using G = TileF2R<P, S1, S2, S3>;
-  apply3d_f32r_batched<P, S1, S2, S3, STIFF, PD>
+  apply3d_f32r_batched<P, S1, S2, S3, STIFF, PD, BF>
       <<<blocks, G::NT, G::smem_floats(STIFF) * sizeof(float), s>>>(bp);
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, int PD>
+template <int P, int S1, int S2, int S3, int PD, bool BF>
 cudaError_t prepare_apply3d_f32r() {
   using G = TileF2R<P, S1, S2, S3>;
   const int sm = (int)(G::smem_floats(false) * sizeof(float));
   const int sk = (int)(G::smem_floats(true) * sizeof(float));
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, false, PD>, a, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, true, PD>, a, sk);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, false, PD>, a, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, true, PD>, a, sk);
+  cudaError_t e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, false, PD, BF>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, true, PD, BF>, a, sk);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF>, a, sk);
   return e;
 }
 
-template <int P, int S1, int S2, int S3, int PD = 2>
+// BF = true: the same kernel reading bfloat16-stored factors.
+template <int P, int S1, int S2, int S3, bool BF = false, int PD = 2>
 ApplyKernel make_apply3d_f32r() {
   using G = TileF2R<P, S1, S2, S3>;
   static_assert(G::NT <= 1024, "tile too large for one block");
@@ -455,11 +463,11 @@ ApplyKernel make_apply3d_f32r() {
   k.plane = G::PL;
   k.lanes = 2;
   k.variant = IGASF_KERNEL_REGISTERS;
-  k.launch[IGASF_MASS] = &launch_apply3d_f32r<P, S1, S2, S3, false, PD>;
-  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32r<P, S1, S2, S3, true, PD>;
-  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, false, PD>;
-  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, true, PD>;
-  k.prepare = &prepare_apply3d_f32r<P, S1, S2, S3, PD>;
+  k.launch[IGASF_MASS] = &launch_apply3d_f32r<P, S1, S2, S3, false, PD, BF>;
+  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32r<P, S1, S2, S3, true, PD, BF>;
+  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF>;
+  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF>;
+  k.prepare = &prepare_apply3d_f32r<P, S1, S2, S3, PD, BF>;
   return k;
 }
 

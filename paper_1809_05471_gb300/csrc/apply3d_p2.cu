@@ -1,6 +1,7 @@
 // 3D apply kernels of order p = 2. FP64: scalar kernel, tile 8, 8, 8 elements.
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
-// of tile shapes and factor-stream variants on the order-sweep workload):
+// of tile shapes and factor-stream variants on the order-sweep workload);
+// BF16 (bfloat16-stored factors) uses the same candidates:
 //   register prefetch, tile 8, 8, 2
 //   register prefetch, tile 8, 8, 4
 //   TMA ring, tile 16, 8, 4
@@ -17,23 +18,24 @@ int apply3d_p2(int prec, ApplyKernel *out, int max_out) {
     if (n < max_out) out[n++] = make_apply3d<double, 2, 8, 8, 8>();
     return n;
   }
+  const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = make_apply3d_f32r<2, 8, 8, 2>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<2, 8, 8, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32<2, 16, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 2, true>() : make_apply3d_f32r<2, 8, 8, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 4, true>() : make_apply3d_f32r<2, 8, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<2, 16, 8, 4, true>() : make_apply3d_f32<2, 16, 8, 4>();
 #else
-  if (n < max_out) out[n++] = make_apply3d_f32r<2, 8, 8, 2>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<2, 8, 8, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<2, 16, 8, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<2, 8, 4, 8>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<2, 8, 8, 8>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<2, 16, 8, 2>();
-  if (n < max_out) out[n++] = make_apply3d_f32<2, 8, 8, 2>();
-  if (n < max_out) out[n++] = make_apply3d_f32<2, 8, 8, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32<2, 16, 8, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32<2, 8, 4, 8>();
-  if (n < max_out) out[n++] = make_apply3d_f32<2, 8, 8, 8>();
-  if (n < max_out) out[n++] = make_apply3d_f32<2, 16, 8, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 2, true>() : make_apply3d_f32r<2, 8, 8, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 4, true>() : make_apply3d_f32r<2, 8, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 16, 8, 4, true>() : make_apply3d_f32r<2, 16, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 4, 8, true>() : make_apply3d_f32r<2, 8, 4, 8>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 8, true>() : make_apply3d_f32r<2, 8, 8, 8>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 16, 8, 2, true>() : make_apply3d_f32r<2, 16, 8, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<2, 8, 8, 2, true>() : make_apply3d_f32<2, 8, 8, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<2, 8, 8, 4, true>() : make_apply3d_f32<2, 8, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<2, 16, 8, 4, true>() : make_apply3d_f32<2, 16, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<2, 8, 4, 8, true>() : make_apply3d_f32<2, 8, 4, 8>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<2, 8, 8, 8, true>() : make_apply3d_f32<2, 8, 8, 8>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<2, 16, 8, 2, true>() : make_apply3d_f32<2, 16, 8, 2>();
 #endif
   return n;
 }

@@ -1,6 +1,7 @@
 // 3D apply kernels of order p = 3. FP64: scalar kernel, tile 8, 4, 4 elements.
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
-// of tile shapes and factor-stream variants on the order-sweep workload):
+// of tile shapes and factor-stream variants on the order-sweep workload);
+// BF16 (bfloat16-stored factors) uses the same candidates:
 //   TMA ring, tile 8, 8, 4
 //   register prefetch, tile 8, 4, 4
 //   register prefetch, tile 4, 4, 4
@@ -17,23 +18,24 @@ int apply3d_p3(int prec, ApplyKernel *out, int max_out) {
     if (n < max_out) out[n++] = make_apply3d<double, 3, 8, 4, 4>();
     return n;
   }
+  const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = make_apply3d_f32<3, 8, 8, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<3, 8, 4, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<3, 4, 4, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32<3, 8, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 4, 4, true>() : make_apply3d_f32r<3, 8, 4, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 4, true>() : make_apply3d_f32r<3, 4, 4, 4>();
 #else
-  if (n < max_out) out[n++] = make_apply3d_f32<3, 8, 8, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<3, 8, 4, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<3, 4, 4, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<3, 8, 8, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<3, 8, 8, 2>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<3, 4, 4, 2>();
-  if (n < max_out) out[n++] = make_apply3d_f32r<3, 8, 4, 2>();
-  if (n < max_out) out[n++] = make_apply3d_f32<3, 8, 4, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32<3, 4, 4, 4>();
-  if (n < max_out) out[n++] = make_apply3d_f32<3, 8, 8, 2>();
-  if (n < max_out) out[n++] = make_apply3d_f32<3, 4, 4, 2>();
-  if (n < max_out) out[n++] = make_apply3d_f32<3, 8, 4, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32<3, 8, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 4, 4, true>() : make_apply3d_f32r<3, 8, 4, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 4, true>() : make_apply3d_f32r<3, 4, 4, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 8, 2, true>() : make_apply3d_f32r<3, 8, 8, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 2, true>() : make_apply3d_f32r<3, 4, 4, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 4, 2, true>() : make_apply3d_f32r<3, 8, 4, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 4, 4, true>() : make_apply3d_f32<3, 8, 4, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 4, 4, 4, true>() : make_apply3d_f32<3, 4, 4, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 2, true>() : make_apply3d_f32<3, 8, 8, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 4, 4, 2, true>() : make_apply3d_f32<3, 4, 4, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 4, 2, true>() : make_apply3d_f32<3, 8, 4, 2>();
 #endif
   return n;
 }

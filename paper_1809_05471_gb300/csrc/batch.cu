@@ -168,7 +168,7 @@ int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, 
   using namespace igasf;
   if (!out || !plans || nplans < 1) return set_error(IGASF_ERR_INVALID_ARG, "need nplans >= 1, plans and out");
   if (op != IGASF_MASS && op != IGASF_STIFFNESS) return set_error(IGASF_ERR_INVALID_ARG, "bad op");
-  if (prec != IGASF_FP64 && prec != IGASF_FP32) return set_error(IGASF_ERR_INVALID_ARG, "bad prec");
+  if (prec < 0 || prec >= kNumPrec) return set_error(IGASF_ERR_INVALID_ARG, "bad prec");
   for (int i = 0; i < nplans; ++i) {
     const igasf_plan *h = plans[i];
     if (!h) return set_error(IGASF_ERR_INVALID_ARG, "a plan is NULL");
@@ -276,7 +276,7 @@ int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, 
       const cudaError_t le = G.k.launch_batched[op](bp, G.blocks, b->cap);
       if (le != cudaSuccess && e == cudaSuccess) e = le;
     }
-    if (prec == IGASF_FP32)
+    if (vectors_are_float(prec))
       batched_gather_kernel<float><<<b->gblocks, kGatherThreads, 0, b->cap>>>(b->d_gp, b->d_gblock_patch,
                                                                             b->d_gfirst);
     else

@@ -69,7 +69,7 @@ void free_plan(igasf_plan *h) {
   delete h;
 }
 
-size_t prec_size(int prec) { return prec == IGASF_FP64 ? sizeof(double) : sizeof(float); }
+size_t prec_size(int prec) { return vector_bytes(prec); }
 
 // Validate one open knot vector; count elements. Returns IGASF_OK or an error.
 int check_knots(int dir, int p, int nk, const double *t, int *K_out) {
@@ -174,7 +174,7 @@ int apply_with_workspace(igasf_plan *h, int op, int prec, const void *u, void *v
   prm.skip_slab = h->skip_slab;
   cudaError_t e = var.k.launch[op](prm, s);
   if (e != cudaSuccess) return cuda_fail(e, "apply kernel launch");
-  e = launch_gather(h->d, prec == IGASF_FP32, ws, v, h->N, var.T, var.k.S, h->p, s);
+  e = launch_gather(h->d, vectors_are_float(prec), ws, v, h->N, var.T, var.k.S, h->p, s);
   if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
   return IGASF_OK;
 }
@@ -209,10 +209,10 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     if (r != 0) return fail(IGASF_ERR_INVALID_ARG, "options.reserved must be zero");
   if (o.kernel_variant < 0 || o.kernel_variant > IGASF_KERNEL_RING)
     return fail(IGASF_ERR_INVALID_ARG, "options.kernel_variant = %d", o.kernel_variant);
-  if (o.default_prec != IGASF_FP64 && o.default_prec != IGASF_FP32)
+  if (o.default_prec < 0 || o.default_prec >= kNumPrec)
     return fail(IGASF_ERR_INVALID_ARG, "options.default_prec = %d", o.default_prec);
   unsigned precs = o.precisions ? o.precisions : IGASF_PREC_BIT(o.default_prec);
-  if (precs & ~(IGASF_PREC_BIT(IGASF_FP64) | IGASF_PREC_BIT(IGASF_FP32)))
+  if (precs & ~((1u << kNumPrec) - 1u))
     return fail(IGASF_ERR_INVALID_ARG, "options.precisions has unknown bits 0x%x", precs);
   if (!(precs & IGASF_PREC_BIT(o.default_prec)))
     return fail(IGASF_ERR_INVALID_ARG, "options.precisions must include default_prec");
@@ -309,11 +309,11 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     }
     v.L.plane = v.k.plane;
     v.L.lanes = v.k.lanes;
-    v.L.is_fp32 = prec == IGASF_FP32;
+    v.L.elem_bytes = factor_bytes(prec);
     const int64_t Qlast = (int64_t)v.k.S[d - 1] * p;
     const int64_t rows = (int64_t)v.ntiles * Qlast;
-    v.bytesM = (size_t)rows * 1 * v.L.plane * es;
-    v.bytesK = (size_t)rows * num_fields(d, IGASF_STIFFNESS) * v.L.plane * es;
+    v.bytesM = (size_t)rows * 1 * v.L.plane * v.L.elem_bytes;
+    v.bytesK = (size_t)rows * num_fields(d, IGASF_STIFFNESS) * v.L.plane * v.L.elem_bytes;
     TRY(alloc(&v.L.DM, v.bytesM, "mass factors"));
     TRY(alloc(&v.L.DK, v.bytesK, "stiffness factors"));
     TRY_CUDA(cudaMemsetAsync(v.L.DM, 0, v.bytesM, s), "memset");
@@ -321,8 +321,10 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     for (int a = 0; a < d; ++a) {
       TRY(alloc(&v.tabB[a], es * p * v.Qpad[a], "tables"));
       TRY(alloc(&v.tabD[a], es * p * v.Qpad[a], "tables"));
-      TRY_CUDA(launch_pad_tables(p, K[a], v.Qpad[a], h->tabB[a], v.tabB[a], v.L.is_fp32, s), "pad tables");
-      TRY_CUDA(launch_pad_tables(p, K[a], v.Qpad[a], h->tabD[a], v.tabD[a], v.L.is_fp32, s), "pad tables");
+      TRY_CUDA(launch_pad_tables(p, K[a], v.Qpad[a], h->tabB[a], v.tabB[a], vectors_are_float(prec), s),
+               "pad tables");
+      TRY_CUDA(launch_pad_tables(p, K[a], v.Qpad[a], h->tabD[a], v.tabD[a], vectors_are_float(prec), s),
+               "pad tables");
     }
     v.vpart_bytes = (size_t)v.ntiles * vol * es;
     TRY(alloc(&v.vpart, v.vpart_bytes, "workspace"));
@@ -425,7 +427,7 @@ int igasf_apply_prec(igasf_handle h, int op, int prec, const void *u, void *v, v
   cudaError_t e = var.k.launch[op](prm, s);
   if (e != cudaSuccess) return cuda_fail(e, "apply kernel launch");
   if (ev) cudaEventRecord(ev[1], s);
-  e = launch_gather(h->d, prec == IGASF_FP32, var.vpart, v, h->N, var.T, var.k.S, h->p, s);
+  e = launch_gather(h->d, vectors_are_float(prec), var.vpart, v, h->N, var.T, var.k.S, h->p, s);
   if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
   if (ev) cudaEventRecord(ev[2], s);
   return IGASF_OK;

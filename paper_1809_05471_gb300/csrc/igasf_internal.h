@@ -10,11 +10,17 @@
 namespace igasf {
 
 constexpr int kMaxDim = 3;
-constexpr int kNumPrec = 2;        // FP64, FP32
+constexpr int kNumPrec = 3;        // FP64, FP32, BF16
 constexpr int kFieldsK3 = 6;       // 11 12 13 22 23 33
 constexpr int kFieldsK2 = 3;       // 11 12 22
 
 inline int num_fields(int d, int op) { return op == IGASF_MASS ? 1 : (d == 3 ? kFieldsK3 : kFieldsK2); }
+
+// Vectors and tables are double for FP64 and float otherwise; factors are
+// stored as double, float or bfloat16.
+inline bool vectors_are_float(int prec) { return prec != IGASF_FP64; }
+inline size_t vector_bytes(int prec) { return prec == IGASF_FP64 ? 8 : 4; }
+inline int factor_bytes(int prec) { return prec == IGASF_FP64 ? 8 : (prec == IGASF_FP32 ? 4 : 2); }
 
 // Arguments of one apply launch; pointers are device addresses in the
 // precision of the kernel (float or double).
@@ -72,7 +78,7 @@ struct FactorLayout {
   int T[kMaxDim];
   int plane;
   int lanes;
-  int is_fp32;
+  int elem_bytes;             // 8 (double), 4 (float) or 2 (bfloat16)
   void *DM;                   // mass factors (1 field)
   void *DK;                   // stiffness factors (num_fields)
 };
@@ -97,11 +103,11 @@ struct GeometryParams {
 cudaError_t launch_tables(int p, int K, const double *knots, const int *span, double *nodes,
                           double *weights, double *tabB, double *tabD, cudaStream_t s);
 cudaError_t launch_geometry(const GeometryParams &g, cudaStream_t s);
-cudaError_t launch_pad_tables(int p, int K, int Qpad, const double *src, void *dst, int is_fp32,
+cudaError_t launch_pad_tables(int p, int K, int Qpad, const double *src, void *dst, int to_float,
                               cudaStream_t s);
 cudaError_t launch_export_factors(const FactorLayout &L, int op, int64_t Qtot, const int *Q,
                                   double *out, cudaStream_t s);
-cudaError_t launch_gather(int d, int is_fp32, const void *vpart, void *v, const int *N,
+cudaError_t launch_gather(int d, int float_vectors, const void *vpart, void *v, const int *N,
                           const int *T, const int *S, int p, cudaStream_t s);
 
 }  // namespace igasf

@@ -14,7 +14,7 @@ int apply3d_p9(int prec, ApplyKernel *out, int max_out);
 ApplyKernel apply2d_any(int p, int prec);
 
 int list_apply_kernels(int d, int p, int prec, ApplyKernel *out, int max_out) {
-  if (prec != IGASF_FP64 && prec != IGASF_FP32) return 0;
+  if (prec < 0 || prec >= kNumPrec) return 0;
   if (p < 2 || p > IGASF_MAX_ORDER || max_out < 1) return 0;
   if (d == 2) {
     out[0] = apply2d_any(p, prec);

@@ -1,6 +1,7 @@
 // Setup-time device kernels: univariate tables (Sec. 6.1), geometry factors
 // (Sec. 6.2, Example 1), table padding, factor export, and the gather that
 // accumulates per-tile partial results (eq. loc-basis-change).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -103,10 +104,10 @@ __global__ void pad_tables_kernel(int p, int Q, int Qpad, const double *src, T *
   dst[i] = q < Q ? (T)src[j * Q + q] : T(0);
 }
 
-cudaError_t launch_pad_tables(int p, int K, int Qpad, const double *src, void *dst, int is_fp32,
+cudaError_t launch_pad_tables(int p, int K, int Qpad, const double *src, void *dst, int to_float,
                               cudaStream_t s) {
   const int n = p * Qpad;
-  if (is_fp32)
+  if (to_float)
     pad_tables_kernel<float><<<(n + 255) / 256, 256, 0, s>>>(p, K * p, Qpad, src, (float *)dst);
   else
     pad_tables_kernel<double><<<(n + 255) / 256, 256, 0, s>>>(p, K * p, Qpad, src, (double *)dst);
@@ -134,27 +135,22 @@ __device__ __forceinline__ int64_t layout_index(const FactorLayout &L, int nf, i
       slab = ql;
     }
   }
-  return factor_index(tile, slab, pen, f, nf, L.plane, L.S[L.d - 1] * p, L.lanes,
-                      L.is_fp32 ? 4 : 8);
+  return factor_index(tile, slab, pen, f, nf, L.plane, L.S[L.d - 1] * p, L.lanes, L.elem_bytes);
 }
 
-template <typename T>
-__device__ __forceinline__ void store_factor(void *base, int64_t idx, double v) {
-  static_cast<T *>(base)[idx] = (T)v;
+// One factor, rounded once from FP64 to the stored type (to nearest even).
+__device__ __forceinline__ void store_factor(const FactorLayout &L, void *base, int64_t idx, double v) {
+  if (L.elem_bytes == 8) static_cast<double *>(base)[idx] = v;
+  else if (L.elem_bytes == 4) static_cast<float *>(base)[idx] = __double2float_rn(v);
+  else static_cast<__nv_bfloat16 *>(base)[idx] = __double2bfloat16(v);
 }
 
 __device__ void write_factors(const GeometryParams &g, const int *qg, double dm, const double *dk,
                               int nfk) {
   for (int o = 0; o < g.nout; ++o) {
     const FactorLayout &L = g.out[o];
-    const int64_t im = layout_index(L, 1, 0, qg);
-    if (L.is_fp32) store_factor<float>(L.DM, im, dm);
-    else store_factor<double>(L.DM, im, dm);
-    for (int f = 0; f < nfk; ++f) {
-      const int64_t ik = layout_index(L, nfk, f, qg);
-      if (L.is_fp32) store_factor<float>(L.DK, ik, dk[f]);
-      else store_factor<double>(L.DK, ik, dk[f]);
-    }
+    store_factor(L, L.DM, layout_index(L, 1, 0, qg), dm);
+    for (int f = 0; f < nfk; ++f) store_factor(L, L.DK, layout_index(L, nfk, f, qg), dk[f]);
   }
 }
 
@@ -358,6 +354,10 @@ cudaError_t launch_geometry(const GeometryParams &g, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Export of stored factors to FP64 in lexicographic quadrature order.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return (double)x; }
+__device__ __forceinline__ double to_double(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
 template <typename T>
 __global__ void export_kernel(const FactorLayout L, int nf, const void *src, int64_t Qtot,
                               int Q0, int Q1, int Q2, double *out) {
@@ -368,7 +368,7 @@ __global__ void export_kernel(const FactorLayout L, int nf, const void *src, int
   qg[1] = (int)((q / Q0) % Q1);
   qg[2] = (int)(q / ((int64_t)Q0 * Q1));
   (void)Q2;
-  for (int f = 0; f < nf; ++f) out[q * nf + f] = (double)static_cast<const T *>(src)[layout_index(L, nf, f, qg)];
+  for (int f = 0; f < nf; ++f) out[q * nf + f] = to_double(static_cast<const T *>(src)[layout_index(L, nf, f, qg)]);
 }
 
 cudaError_t launch_export_factors(const FactorLayout &L, int op, int64_t Qtot, const int *Q,
@@ -377,7 +377,9 @@ cudaError_t launch_export_factors(const FactorLayout &L, int op, int64_t Qtot, c
   const void *src = op == IGASF_MASS ? L.DM : L.DK;
   const unsigned blocks = (unsigned)((Qtot + 255) / 256);
   const int Q2 = L.d > 2 ? Q[2] : 1, Q1 = L.d > 1 ? Q[1] : 1;
-  if (L.is_fp32) export_kernel<float><<<blocks, 256, 0, s>>>(L, nf, src, Qtot, Q[0], Q1, Q2, out);
+  if (L.elem_bytes == 4) export_kernel<float><<<blocks, 256, 0, s>>>(L, nf, src, Qtot, Q[0], Q1, Q2, out);
+  else if (L.elem_bytes == 2)
+    export_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(L, nf, src, Qtot, Q[0], Q1, Q2, out);
   else export_kernel<double><<<blocks, 256, 0, s>>>(L, nf, src, Qtot, Q[0], Q1, Q2, out);
   return cudaGetLastError();
 }
@@ -434,7 +436,7 @@ __global__ void gather_kernel(const T *__restrict__ vpart, T *__restrict__ v, in
   v[n] = acc;
 }
 
-cudaError_t launch_gather(int d, int is_fp32, const void *vpart, void *v, const int *N,
+cudaError_t launch_gather(int d, int float_vectors, const void *vpart, void *v, const int *N,
                           const int *T, const int *S, int p, cudaStream_t s) {
   const int N1 = d > 1 ? N[1] : 1, N2 = d > 2 ? N[2] : 1;
   const int T1 = d > 1 ? T[1] : 1, T2 = d > 2 ? T[2] : 1;
@@ -447,7 +449,7 @@ cudaError_t launch_gather(int d, int is_fp32, const void *vpart, void *v, const 
 #define IGASF_GATHER(TT, TWO_)                                                                 \
   gather_kernel<TT, TWO_><<<blocks, 256, 0, s>>>((const TT *)vpart, (TT *)v, N[0], N1, Ntot, T[0], \
                                                  T1, T2, S[0], S1, S2, E0, E1, E2, vol)
-  if (is_fp32) {
+  if (float_vectors) {
     if (two) IGASF_GATHER(float, true);
     else IGASF_GATHER(float, false);
   } else {

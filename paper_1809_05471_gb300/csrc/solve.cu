@@ -323,8 +323,8 @@ extern "C" int igasf_cg_solve(igasf_handle h, int inner_prec, const double *b, d
   using namespace igasf;
   if (!h || !b || !x) return set_error(IGASF_ERR_INVALID_ARG, "handle, b and x must be non-NULL");
   if (h->d != 3) return set_error(IGASF_ERR_UNSUPPORTED, "the solver handles d = 3 plans");
-  if (inner_prec != IGASF_FP64 && inner_prec != IGASF_FP32)
-    return set_error(IGASF_ERR_INVALID_ARG, "inner_prec must be IGASF_FP64 or IGASF_FP32");
+  if (inner_prec < 0 || inner_prec >= kNumPrec)
+    return set_error(IGASF_ERR_INVALID_ARG, "inner_prec must be IGASF_FP64, IGASF_FP32 or IGASF_BF16");
   if (!h->var[IGASF_FP64].present || !h->var[inner_prec].present)
     return set_error(IGASF_ERR_UNSUPPORTED, "the solve needs FP64 (and the inner precision) stored");
   if (!(rtol > 0.0) || !(inner_rtol > 0.0 && inner_rtol < 1.0) || max_iterations < 1)
@@ -388,7 +388,7 @@ extern "C" int igasf_cg_solve(igasf_handle h, int inner_prec, const double *b, d
   double **d64[] = {&w.r, &w.z, &w.pv, &w.q, &w.kx};
   for (double **pp : d64)
     if (e == cudaSuccess) e = cudaMalloc((void **)pp, sizeof(double) * n);
-  if (inner_prec == IGASF_FP32) {
+  if (inner_prec != IGASF_FP64) {
     float **f32[] = {&w.d32, &w.r32, &w.z32, &w.p32, &w.q32};
     for (float **pp : f32)
       if (e == cudaSuccess) e = cudaMalloc((void **)pp, sizeof(float) * n);
@@ -416,7 +416,7 @@ extern "C" int igasf_cg_solve(igasf_handle h, int inner_prec, const double *b, d
     bnorm = rn;
     while (ok && rn > rtol * bnorm && rep.inner_iterations < max_iterations) {
       int it_before = rep.inner_iterations;
-      ok = pcg<float, double>(c, IGASF_FP32, w.r, w.d32, w.r32, w.z32, w.p32, w.q32, h->dinv32,
+      ok = pcg<float, double>(c, inner_prec, w.r, w.d32, w.r32, w.z32, w.p32, w.q32, h->dinv32,
                               inner_rtol, max_iterations - rep.inner_iterations,
                               &rep.inner_iterations, nullptr);
       if (!ok) break;

@@ -20,6 +20,7 @@ MASS = 0
 STIFFNESS = 1
 FP64 = 0
 FP32 = 1
+BF16 = 2        # bfloat16-stored factors, float32 vectors and arithmetic
 COEF_CONSTANT = 0
 COEF_EXP_SIN_COS = 1
 COEF_VALUES = 2
@@ -192,7 +193,7 @@ class Plan:
         return self.handle
 
     def apply(self, op: int, u, v, prec: int = FP64, stream=None):
-        """v = A u on device tensors (float64 for FP64, float32 for FP32)."""
+        """v = A u on device tensors (float64 for FP64, float32 for FP32 and BF16)."""
         _check(load_library().igasf_apply_prec(self._h(), int(op), int(prec), u.data_ptr(),
                                                v.data_ptr(), _stream_handle(stream)))
         return v

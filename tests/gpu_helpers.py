@@ -9,7 +9,7 @@ from paper_1809_05471_gb300 import igasf as G
 from paper_1809_05471_gb300 import inputs as I
 
 TOL = {G.FP64: 1e-12, G.FP32: 1e-5}
-DTYPE = {G.FP64: "float64", G.FP32: "float32"}
+DTYPE = {G.FP64: "float64", G.FP32: "float32", G.BF16: "float32"}
 
 
 def gpu_apply(plan, op, u, prec):

@@ -22,15 +22,15 @@ def _small_batch(n, seed):
     return out
 
 
-@pytest.mark.parametrize("prec", [G.FP32, G.FP64])
+@pytest.mark.parametrize("prec", [G.FP32, G.FP64, G.BF16])
 def test_batch_equals_individual_applies(prec):
     import torch
-    dt = torch.float32 if prec == G.FP32 else torch.float64
+    dt = torch.float64 if prec == G.FP64 else torch.float32
     patches = _small_batch(12, 3)
     # force two kernel variants on patches of the same order to get several groups
     plans = []
     for i, (pt, _) in enumerate(patches):
-        kv = G.KERNEL_RING if (prec == G.FP32 and i % 2) else 0
+        kv = G.KERNEL_RING if (prec != G.FP64 and i % 2) else 0
         plans.append(G.Plan.from_patch(pt, precisions=(prec,), kernel_variant=kv))
     u = np.concatenate([u for _, u in patches])
     ud = torch.as_tensor(u, device="cuda").to(dt)
@@ -53,10 +53,11 @@ def test_batch_equals_individual_applies(prec):
         for k in (0, 5):
             pt, uk = patches[k]
             rows = sample_rows(pt, 16, seed=k)
-            vr, ra = O.apply_rows(pt, O.STIFFNESS, uk, rows)
+            with O.stored_factor_bits(O.BF16_BITS if prec == G.BF16 else 0):
+                vr, ra = O.apply_rows(pt, O.STIFFNESS, uk, rows)
             a = batch.offsets[k]
             vk = v[a:a + pt.num_dofs].double().cpu().numpy()[rows]
-            assert scaled_err(vk, vr, ra.max(), uk) < TOL[prec]
+            assert scaled_err(vk, vr, ra.max(), uk) < TOL[G.FP32 if prec == G.BF16 else prec]
     for plan in plans:
         assert plan.device_status() == 0
         plan.close()

@@ -7,6 +7,7 @@ hang is involved: the missing slab is simply never requested."""
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1809_05471_gb300 import igasf as G
 from paper_1809_05471_gb300 import inputs as I
 from tests.gpu_helpers import TOL, oracle_full, scaled_err
@@ -14,22 +15,24 @@ from tests.gpu_helpers import TOL, oracle_full, scaled_err
 pytestmark = pytest.mark.gpu
 
 
-def test_missing_slab_times_out_and_reports_status():
+@pytest.mark.parametrize("prec", [G.FP32, G.BF16], ids=["fp32", "bf16"])
+def test_missing_slab_times_out_and_reports_status(prec):
     import torch
     patch, u = I.config_cube(p=4, K=9)
-    v_ref, a_inf = oracle_full(patch, G.STIFFNESS, u)
-    with G.Plan.from_patch(patch, precisions=(G.FP32,), kernel_variant=G.KERNEL_RING) as plan:
-        assert plan.describe(G.FP32)["kernel_variant"] == G.KERNEL_RING
+    with O.stored_factor_bits(O.BF16_BITS if prec == G.BF16 else 0):
+        v_ref, a_inf = oracle_full(patch, G.STIFFNESS, u)
+    with G.Plan.from_patch(patch, precisions=(prec,), kernel_variant=G.KERNEL_RING) as plan:
+        assert plan.describe(prec)["kernel_variant"] == G.KERNEL_RING
         ud = torch.as_tensor(u, device="cuda").float()
         v = torch.empty_like(ud)
         assert plan.device_status() == 0
         plan.set_test_fault(skip_slab=3, wait_limit_cycles=200000)
-        plan.apply(G.STIFFNESS, ud, v, prec=G.FP32)
+        plan.apply(G.STIFFNESS, ud, v, prec=prec)
         assert plan.device_status(clear=True) == -7          # IGASF_ERR_TIMEOUT
         assert plan.device_status() == 0                     # cleared
         plan.set_test_fault(skip_slab=-1)
         for apply in (plan.apply, plan.apply_noalloc):
-            apply(G.STIFFNESS, ud, v, prec=G.FP32)
+            apply(G.STIFFNESS, ud, v, prec=prec)
             assert plan.device_status() == 0
             assert scaled_err(v.double().cpu().numpy(), v_ref, a_inf, u) < TOL[G.FP32]
 
