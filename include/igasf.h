@@ -329,6 +329,37 @@ int igasf_autotune(int d, const int *orders, const int *knot_lengths, const doub
                    const double *ctrl, const igasf_coef *coef, int op, int prec, int repeats,
                    int *tile, int *kernel_variant, double *best_ms);
 
+/*
+ * Number of stored entries of the assembled matrix: the pairs (m, n) with
+ * |m_a - n_a| <= p - 1 in every direction, which for simple interior knots is
+ * prod_a ((2p - 1) K_a + (p - 1)^2) (Sec. 3.2, Corollary on nnz of B-spline
+ * matrices). Returns a negative status on error.
+ */
+int64_t igasf_assembled_nnz(igasf_handle h);
+
+/*
+ * Assembles the matrix of `op` (the quadrature operator itself, eq.
+ * quadrature:1) in FP64 CSR on the device by sum factorization over the whole
+ * patch (Sec. 3, Alg. 1: the sums over the quadrature points of direction 1,
+ * then 2, then d are carried out one direction at a time, with the partial
+ * results of each level kept for all pairs of the later directions).
+ * Intermediate levels are processed in chunks of element layers along the
+ * last direction, so that they stay within `workspace_limit_bytes` of device
+ * memory (0 = 2 GiB); every chunk adds to the values in a fixed order, so the
+ * result is bitwise reproducible.
+ *
+ *   rowptr  device, num_dofs + 1 int64 (rowptr[0] = 0)
+ *   colind  device, nnz int64, ascending within each row (lexicographic dof
+ *           numbering, first index fastest)
+ *   values  device, nnz doubles
+ * nnz = igasf_assembled_nnz(h); the arrays are caller-owned, 8-byte aligned.
+ * Uses the plan's FP64 factors w F (the plan must store FP64). Synchronous on
+ * `stream`; allocates its workspace for the duration of the call. Errors:
+ * INVALID_ARG, UNSUPPORTED (FP64 not stored), CUDA, OOM.
+ */
+int igasf_assemble_csr(igasf_handle h, int op, int64_t *rowptr, int64_t *colind, double *values,
+                       size_t workspace_limit_bytes, void *stream);
+
 /* Message for the last error on this host thread ("" if none). */
 const char *igasf_last_error_message(void);
 

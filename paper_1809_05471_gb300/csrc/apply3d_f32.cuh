@@ -61,6 +61,104 @@ __device__ __forceinline__ float4 widen(uint2 c) {
 }
 __device__ __forceinline__ float2 widen(uint32_t c) { return bf16x2_to_float2(c); }
 
+// ---- staging of one tile: the tables of the three directions and the u box
+// (the selection S_D u of eq. loc-basis-change). Every global load of a thread
+// is issued through the read-only path before its first shared-memory store,
+// so the block waits for one round of load latency instead of one per loop
+// trip. Tables of directions 2 and 3 are stored as duplicated pairs {b, b},
+// padded with zeros to PP entries per quadrature point.
+template <int P, int S1, int S2, int S3, int NT, bool STIFF>
+__device__ __forceinline__ void stage_tile_f32(const ApplyParams &prm, const int tid, const int e01,
+                                               const int e02, const int e03, float *t1b, float *t1d,
+                                               float *t2b, float *t2d, float *t3b, float *t3d,
+                                               float *us) {
+  constexpr int E1 = S1 + P - 1, E2 = S2 + P - 1, E3 = S3 + P - 1;
+  constexpr int Q1 = S1 * P, Q2 = S2 * P, Q3 = S3 * P, PP = P + (P & 1);
+  constexpr int VOL = E1 * E2 * E3;
+  constexpr int A1 = (P * Q1 + NT - 1) / NT, A2 = (PP * Q2 + NT - 1) / NT;
+  constexpr int A3 = (PP * Q3 + NT - 1) / NT, AU = (VOL + NT - 1) / NT;
+  const float *gb1 = static_cast<const float *>(prm.tabB[0]), *gd1 = static_cast<const float *>(prm.tabD[0]);
+  const float *gb2 = static_cast<const float *>(prm.tabB[1]), *gd2 = static_cast<const float *>(prm.tabD[1]);
+  const float *gb3 = static_cast<const float *>(prm.tabB[2]), *gd3 = static_cast<const float *>(prm.tabD[2]);
+  const float *u = static_cast<const float *>(prm.u);
+  float b1[A1], d1[A1], b2[A2], d2[A2], b3[A3], d3[A3], uv[AU];
+#pragma unroll
+  for (int k = 0; k < A1; ++k) {
+    const int i = tid + k * NT;
+    b1[k] = 0.f;
+    d1[k] = 0.f;
+    if (i < P * Q1) {
+      const int j = i / Q1, q = i - j * Q1;
+      const int g = j * prm.Qpad[0] + e01 * P + q;
+      b1[k] = __ldg(gb1 + g);
+      if (STIFF) d1[k] = __ldg(gd1 + g);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < A2; ++k) {
+    const int i = tid + k * NT;
+    const int q = i / PP, j = i - q * PP;
+    b2[k] = 0.f;
+    d2[k] = 0.f;
+    if (i < PP * Q2 && j < P) {
+      const int g = j * prm.Qpad[1] + e02 * P + q;
+      b2[k] = __ldg(gb2 + g);
+      if (STIFF) d2[k] = __ldg(gd2 + g);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < A3; ++k) {
+    const int i = tid + k * NT;
+    const int q = i / PP, j = i - q * PP;
+    b3[k] = 0.f;
+    d3[k] = 0.f;
+    if (i < PP * Q3 && j < P) {
+      const int g = j * prm.Qpad[2] + e03 * P + q;
+      b3[k] = __ldg(gb3 + g);
+      if (STIFF) d3[k] = __ldg(gd3 + g);
+    }
+  }
+  const int N1 = prm.N[0], N2 = prm.N[1], N3 = prm.N[2];
+#pragma unroll
+  for (int k = 0; k < AU; ++k) {
+    const int i = tid + k * NT;
+    const int n1 = i % E1, r = i / E1;
+    const int n2 = r % E2, n3 = r / E2;
+    const int g1 = e01 + n1, g2 = e02 + n2, g3 = e03 + n3;
+    uv[k] = 0.f;
+    if (i < VOL && g1 < N1 && g2 < N2 && g3 < N3) uv[k] = __ldg(u + ((int64_t)g3 * N2 + g2) * N1 + g1);
+  }
+#pragma unroll
+  for (int k = 0; k < A1; ++k) {
+    const int i = tid + k * NT;
+    if (i < P * Q1) {
+      t1b[i] = b1[k];
+      if (STIFF) t1d[i] = d1[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < A2; ++k) {
+    const int i = tid + k * NT;
+    if (i < PP * Q2) {
+      reinterpret_cast<float2 *>(t2b)[i] = make_float2(b2[k], b2[k]);
+      if (STIFF) reinterpret_cast<float2 *>(t2d)[i] = make_float2(d2[k], d2[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < A3; ++k) {
+    const int i = tid + k * NT;
+    if (i < PP * Q3) {
+      reinterpret_cast<float2 *>(t3b)[i] = make_float2(b3[k], b3[k]);
+      if (STIFF) reinterpret_cast<float2 *>(t3d)[i] = make_float2(d3[k], d3[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < AU; ++k) {
+    const int i = tid + k * NT;
+    if (i < VOL) us[i] = uv[k];
+  }
+}
+
 // ---- mbarrier and bulk-copy helpers (shared-memory addresses as 32-bit) ----
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -233,49 +331,8 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
     const int ke3 = min(S3, prm.K[2] - e03);
     const int nslab = ke3 * P;
 
-    // ---- stage tables and the u tile (selection S_D u of eq. loc-basis-change)
-    {
-      const float *gb1 = static_cast<const float *>(prm.tabB[0]), *gd1 = static_cast<const float *>(prm.tabD[0]);
-      const float *gb2 = static_cast<const float *>(prm.tabB[1]), *gd2 = static_cast<const float *>(prm.tabD[1]);
-      const float *gb3 = static_cast<const float *>(prm.tabB[2]), *gd3 = static_cast<const float *>(prm.tabD[2]);
-      for (int i = tid; i < P * Q1; i += NTC) {
-        const int j = i / Q1, q = i - j * Q1;
-        t1b[i] = gb1[j * prm.Qpad[0] + e01 * P + q];
-        if (STIFF) t1d[i] = gd1[j * prm.Qpad[0] + e01 * P + q];
-      }
-      for (int i = tid; i < PP * Q2; i += NTC) {
-        const int q = i / PP, j = i - q * PP;
-        const float b = j < P ? gb2[j * prm.Qpad[1] + e02 * P + q] : 0.f;
-        t2b[2 * i] = b;
-        t2b[2 * i + 1] = b;
-        if (STIFF) {
-          const float db = j < P ? gd2[j * prm.Qpad[1] + e02 * P + q] : 0.f;
-          t2d[2 * i] = db;
-          t2d[2 * i + 1] = db;
-        }
-      }
-      for (int i = tid; i < PP * Q3; i += NTC) {
-        const int q = i / PP, j = i - q * PP;
-        const float b = j < P ? gb3[j * prm.Qpad[2] + e03 * P + q] : 0.f;
-        t3b[2 * i] = b;
-        t3b[2 * i + 1] = b;
-        if (STIFF) {
-          const float db = j < P ? gd3[j * prm.Qpad[2] + e03 * P + q] : 0.f;
-          t3d[2 * i] = db;
-          t3d[2 * i + 1] = db;
-        }
-      }
-      const float *u = static_cast<const float *>(prm.u);
-      const int N1 = prm.N[0], N2 = prm.N[1], N3 = prm.N[2];
-      for (int i = tid; i < G::VOL; i += NTC) {
-        const int n1 = i % E1, r = i / E1;
-        const int n2 = r % E2, n3 = r / E2;
-        const int g1 = e01 + n1, g2 = e02 + n2, g3 = e03 + n3;
-        float val = 0.f;
-        if (g1 < N1 && g2 < N2 && g3 < N3) val = u[((int64_t)g3 * N2 + g2) * N1 + g1];
-        us[i] = val;
-      }
-    }
+    // ---- stage tables and the u tile
+    stage_tile_f32<P, S1, S2, S3, NTC, STIFF>(prm, tid, e01, e02, e03, t1b, t1d, t2b, t2d, t3b, t3d, us);
     consumer_sync(NTC);
 
     // ---- A: direction 1, X0 = B1 u, X1 = B1' u, one pencil pair per item

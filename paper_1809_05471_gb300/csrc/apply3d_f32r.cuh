@@ -32,8 +32,21 @@
 #include "igasf_internal.h"
 #include "layout.h"
 
-namespace igasf {
+// Compile-time knobs of the tile search: slabs prefetched ahead (PD) and the
+// minimum resident blocks per SM requested from the register allocator.
+#ifndef IGASF_F32R_PD
+#define IGASF_F32R_PD 2
+#endif
+#ifndef IGASF_F32R_MINB
+#define IGASF_F32R_MINB 0
+#endif
+#if IGASF_F32R_MINB > 0
+#define IGASF_F32R_BOUNDS(...) __launch_bounds__(__VA_ARGS__, IGASF_F32R_MINB)
+#else
+#define IGASF_F32R_BOUNDS(...) __launch_bounds__(__VA_ARGS__)
+#endif
 
+namespace igasf {
 
 // Streaming (evict-first) loads of one factor chunk.
 __device__ __forceinline__ float4 ldg_stream(const float4 *p) {
@@ -125,49 +138,8 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
     }
   }
 
-  // ---- stage tables and the u tile (selection S_D u of eq. loc-basis-change)
-  {
-    const float *gb1 = static_cast<const float *>(prm.tabB[0]), *gd1 = static_cast<const float *>(prm.tabD[0]);
-    const float *gb2 = static_cast<const float *>(prm.tabB[1]), *gd2 = static_cast<const float *>(prm.tabD[1]);
-    const float *gb3 = static_cast<const float *>(prm.tabB[2]), *gd3 = static_cast<const float *>(prm.tabD[2]);
-    for (int i = tid; i < P * Q1; i += NT) {
-      const int j = i / Q1, q = i - j * Q1;
-      t1b[i] = gb1[j * prm.Qpad[0] + e01 * P + q];
-      if (STIFF) t1d[i] = gd1[j * prm.Qpad[0] + e01 * P + q];
-    }
-    for (int i = tid; i < PP * Q2; i += NT) {
-      const int q = i / PP, j = i - q * PP;
-      const float b = j < P ? gb2[j * prm.Qpad[1] + e02 * P + q] : 0.f;
-      t2b[2 * i] = b;
-      t2b[2 * i + 1] = b;
-      if (STIFF) {
-        const float db = j < P ? gd2[j * prm.Qpad[1] + e02 * P + q] : 0.f;
-        t2d[2 * i] = db;
-        t2d[2 * i + 1] = db;
-      }
-    }
-    for (int i = tid; i < PP * Q3; i += NT) {
-      const int q = i / PP, j = i - q * PP;
-      const float b = j < P ? gb3[j * prm.Qpad[2] + e03 * P + q] : 0.f;
-      t3b[2 * i] = b;
-      t3b[2 * i + 1] = b;
-      if (STIFF) {
-        const float db = j < P ? gd3[j * prm.Qpad[2] + e03 * P + q] : 0.f;
-        t3d[2 * i] = db;
-        t3d[2 * i + 1] = db;
-      }
-    }
-    const float *u = static_cast<const float *>(prm.u);
-    const int N1 = prm.N[0], N2 = prm.N[1], N3 = prm.N[2];
-    for (int i = tid; i < G::VOL; i += NT) {
-      const int n1 = i % E1, r = i / E1;
-      const int n2 = r % E2, n3 = r / E2;
-      const int g1 = e01 + n1, g2 = e02 + n2, g3 = e03 + n3;
-      float val = 0.f;
-      if (g1 < N1 && g2 < N2 && g3 < N3) val = u[((int64_t)g3 * N2 + g2) * N1 + g1];
-      us[i] = val;
-    }
-  }
+  // ---- stage tables and the u tile
+  stage_tile_f32<P, S1, S2, S3, NT, STIFF>(prm, tid, e01, e02, e03, t1b, t1d, t2b, t2d, t3b, t3d, us);
   __syncthreads();
 
   // ---- A: direction 1, X0 = B1 u, X1 = B1' u, one pencil pair per item
@@ -404,7 +376,7 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
 }
 
 template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
-__global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
+__global__ void IGASF_F32R_BOUNDS(TileF2R<P, S1, S2, S3>::NT)
 apply3d_f32r_kernel(const ApplyParams prm) {
   apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(prm, blockIdx.x);
 }
@@ -412,7 +384,7 @@ apply3d_f32r_kernel(const ApplyParams prm) {
 // Many patches in one launch: block b works on tile b - first_block[patch] of
 // patch = block_patch[b], with that patch's parameters.
 template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
-__global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
+__global__ void IGASF_F32R_BOUNDS(TileF2R<P, S1, S2, S3>::NT)
 apply3d_f32r_batched(const BatchParams bp) {
   const int patch = bp.block_patch[blockIdx.x];
   apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
@@ -448,7 +420,7 @@ cudaError_t prepare_apply3d_f32r() {
 }
 
 // BF = true: the same kernel reading bfloat16-stored factors.
-template <int P, int S1, int S2, int S3, bool BF = false, int PD = 2>
+template <int P, int S1, int S2, int S3, bool BF = false, int PD = IGASF_F32R_PD>
 ApplyKernel make_apply3d_f32r() {
   using G = TileF2R<P, S1, S2, S3>;
   static_assert(G::NT <= 1024, "tile too large for one block");

@@ -42,4 +42,27 @@ IGASF_HD int64_t factor_index(int64_t tile, int slab, int pen, int f, int nf, in
   return (((tile * qlast + slab) * nch + ch) * (int64_t)units + unit) * ce + w;
 }
 
+// Index of field f at the quadrature point with per-direction global indices
+// qg[0..d-1], in the layout of tiles of S[a] elements, T[a] tiles per
+// direction: the tile, the pencil inside the tile's slab (directions before
+// the last, first fastest) and the slab (the last direction's local index).
+IGASF_HD int64_t layout_index_q(int d, int p, const int *S, const int *T, int plane, int lanes,
+                                int elem_bytes, int nf, int f, const int *qg) {
+  int64_t tile = 0, stride = 1;
+  int pen = 0, pstride = 1, slab = 0;
+  for (int a = 0; a < d; ++a) {
+    const int t = qg[a] / p / S[a];
+    const int ql = qg[a] - t * S[a] * p;
+    tile += t * stride;
+    stride *= T[a];
+    if (a < d - 1) {
+      pen += ql * pstride;
+      pstride *= S[a] * p;
+    } else {
+      slab = ql;
+    }
+  }
+  return factor_index(tile, slab, pen, f, nf, plane, S[d - 1] * p, lanes, elem_bytes);
+}
+
 }  // namespace igasf

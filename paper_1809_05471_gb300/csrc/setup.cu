@@ -119,23 +119,7 @@ cudaError_t launch_pad_tables(int p, int K, int Qpad, const double *src, void *d
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int64_t layout_index(const FactorLayout &L, int nf, int f,
                                                 const int *qg) {
-  const int p = L.p;
-  int64_t tile = 0, stride = 1;
-  int pen = 0, pstride = 1, slab = 0;
-  for (int a = 0; a < L.d; ++a) {
-    const int e = qg[a] / p;
-    const int t = e / L.S[a];
-    const int ql = qg[a] - t * L.S[a] * p;
-    tile += t * stride;
-    stride *= L.T[a];
-    if (a < L.d - 1) {
-      pen += ql * pstride;
-      pstride *= L.S[a] * p;
-    } else {
-      slab = ql;
-    }
-  }
-  return factor_index(tile, slab, pen, f, nf, L.plane, L.S[L.d - 1] * p, L.lanes, L.elem_bytes);
+  return layout_index_q(L.d, L.p, L.S, L.T, L.plane, L.lanes, L.elem_bytes, nf, f, qg);
 }
 
 // One factor, rounded once from FP64 to the stored type (to nearest even).

@@ -49,21 +49,7 @@ struct DiagParams {
 };
 
 __device__ double factor_k(const DiagParams &g, int f, const int *qg) {
-  const int p = g.p;
-  int64_t tile = 0, stride = 1;
-  int pen = 0, pstride = 1, slab = 0;
-  for (int a = 0; a < 3; ++a) {
-    const int e = qg[a] / p, t = e / g.S[a], ql = qg[a] - t * g.S[a] * p;
-    tile += t * stride;
-    stride *= g.T[a];
-    if (a < 2) {
-      pen += ql * pstride;
-      pstride *= g.S[a] * p;
-    } else {
-      slab = ql;
-    }
-  }
-  return g.DK[factor_index(tile, slab, pen, f, 6, g.plane, g.S[2] * p, g.lanes, 8)];
+  return g.DK[layout_index_q(3, g.p, g.S, g.T, g.plane, g.lanes, 8, 6, f, qg)];
 }
 
 __global__ void diag_kernel(const DiagParams g) {

@@ -40,7 +40,7 @@ EXPORTED = [
     "igasf_get_factors", "igasf_profile_begin", "igasf_profile_end", "igasf_apply_noalloc",
     "igasf_device_status", "igasf_set_test_fault", "igasf_cg_solve",
     "igasf_batch_create", "igasf_batch_apply", "igasf_batch_info", "igasf_batch_destroy",
-    "igasf_autotune",
+    "igasf_autotune", "igasf_assembled_nnz", "igasf_assemble_csr",
     "igasf_last_error_message", "igasf_version",
 ]
 
@@ -114,6 +114,9 @@ def load_library(path: str = LIB_PATH):
     lib.igasf_batch_destroy.argtypes = [vp]
     lib.igasf_autotune.argtypes = [ctypes.c_int, ip, ip, ctypes.POINTER(dp), dp, ctypes.POINTER(Coef),
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip, dp]
+    lib.igasf_assembled_nnz.argtypes = [vp]
+    lib.igasf_assembled_nnz.restype = ctypes.c_int64
+    lib.igasf_assemble_csr.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_size_t, vp]
     lib.igasf_device_status.argtypes = [vp, ctypes.c_int]
     lib.igasf_set_test_fault.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
     lib.igasf_profile_begin.argtypes = [vp, ctypes.c_int]
@@ -258,6 +261,27 @@ class Plan:
                     inner_iterations=rep.inner_iterations, final_relres=rep.final_relres,
                     seconds=rep.seconds)
 
+    def assembled_nnz(self) -> int:
+        """Stored entries of the assembled matrix (Corollary on nnz)."""
+        n = int(load_library().igasf_assembled_nnz(self._h()))
+        if n < 0:
+            _check(n)
+        return n
+
+    def assemble_csr(self, op: int, workspace_limit_bytes: int = 0, stream=None):
+        """FP64 CSR of the operator, assembled on the device by sum
+        factorization (Alg. 1): (rowptr, colind, values) as device tensors
+        (int64, int64, float64). The plan must store FP64."""
+        import torch
+        nnz = self.assembled_nnz()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        rowptr = torch.empty(self.num_dofs + 1, dtype=torch.int64, device=dev)
+        colind = torch.empty(nnz, dtype=torch.int64, device=dev)
+        values = torch.empty(nnz, dtype=torch.float64, device=dev)
+        _check(load_library().igasf_assemble_csr(self._h(), int(op), rowptr.data_ptr(),
+                                                 colind.data_ptr(), values.data_ptr(),
+                                                 int(workspace_limit_bytes), _stream_handle(stream)))
+        return rowptr, colind, values
     def device_status(self, clear: bool = True) -> int:
         """IGASF_OK (0) or IGASF_ERR_TIMEOUT (-7) if a bounded device wait ran out."""
         return int(load_library().igasf_device_status(self._h(), int(clear)))
