@@ -32,20 +32,6 @@
 #include "igasf_internal.h"
 #include "layout.h"
 
-// Compile-time knobs of the tile search: slabs prefetched ahead (PD) and the
-// minimum resident blocks per SM requested from the register allocator.
-#ifndef IGASF_F32R_PD
-#define IGASF_F32R_PD 2
-#endif
-#ifndef IGASF_F32R_MINB
-#define IGASF_F32R_MINB 0
-#endif
-#if IGASF_F32R_MINB > 0
-#define IGASF_F32R_BOUNDS(...) __launch_bounds__(__VA_ARGS__, IGASF_F32R_MINB)
-#else
-#define IGASF_F32R_BOUNDS(...) __launch_bounds__(__VA_ARGS__)
-#endif
-
 namespace igasf {
 
 // Streaming (evict-first) loads of one factor chunk.
@@ -375,52 +361,83 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
   }
 }
 
+// Two kernel entry points per configuration: without a minimum of resident
+// blocks (the register allocator's own choice) and with one (MINB > 0 caps the
+// registers per thread at 65536 / (MINB * threads)); the launch picks by MINB.
 template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
-__global__ void IGASF_F32R_BOUNDS(TileF2R<P, S1, S2, S3>::NT)
+__global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
 apply3d_f32r_kernel(const ApplyParams prm) {
+  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(prm, blockIdx.x);
+}
+
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int MINB>
+__global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT, MINB)
+apply3d_f32r_kernel_mb(const ApplyParams prm) {
   apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(prm, blockIdx.x);
 }
 
 // Many patches in one launch: block b works on tile b - first_block[patch] of
 // patch = block_patch[b], with that patch's parameters.
 template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
-__global__ void IGASF_F32R_BOUNDS(TileF2R<P, S1, S2, S3>::NT)
+__global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
 apply3d_f32r_batched(const BatchParams bp) {
   const int patch = bp.block_patch[blockIdx.x];
   apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int MINB>
+__global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT, MINB)
+apply3d_f32r_batched_mb(const BatchParams bp) {
+  const int patch = bp.block_patch[blockIdx.x];
+  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
+}
+
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int MINB>
 cudaError_t launch_apply3d_f32r(const ApplyParams &prm, cudaStream_t s) {
   using G = TileF2R<P, S1, S2, S3>;
-  apply3d_f32r_kernel<P, S1, S2, S3, STIFF, PD, BF>
-      <<<prm.ntiles, G::NT, G::smem_floats(STIFF) * sizeof(float), s>>>(prm);
+  const size_t sh = G::smem_floats(STIFF) * sizeof(float);
+  if constexpr (MINB > 0)
+    apply3d_f32r_kernel_mb<P, S1, S2, S3, STIFF, PD, BF, MINB><<<prm.ntiles, G::NT, sh, s>>>(prm);
+  else
+    apply3d_f32r_kernel<P, S1, S2, S3, STIFF, PD, BF><<<prm.ntiles, G::NT, sh, s>>>(prm);
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int MINB>
 cudaError_t launch_apply3d_f32r_batched(const BatchParams &bp, int blocks, cudaStream_t s) {
   using G = TileF2R<P, S1, S2, S3>;
-  apply3d_f32r_batched<P, S1, S2, S3, STIFF, PD, BF>
-      <<<blocks, G::NT, G::smem_floats(STIFF) * sizeof(float), s>>>(bp);
+  const size_t sh = G::smem_floats(STIFF) * sizeof(float);
+  if constexpr (MINB > 0)
+    apply3d_f32r_batched_mb<P, S1, S2, S3, STIFF, PD, BF, MINB><<<blocks, G::NT, sh, s>>>(bp);
+  else
+    apply3d_f32r_batched<P, S1, S2, S3, STIFF, PD, BF><<<blocks, G::NT, sh, s>>>(bp);
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, int PD, bool BF>
+template <int P, int S1, int S2, int S3, int PD, bool BF, int MINB>
 cudaError_t prepare_apply3d_f32r() {
   using G = TileF2R<P, S1, S2, S3>;
   const int sm = (int)(G::smem_floats(false) * sizeof(float));
   const int sk = (int)(G::smem_floats(true) * sizeof(float));
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, false, PD, BF>, a, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, true, PD, BF>, a, sk);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF>, a, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF>, a, sk);
+  cudaError_t e;
+  if constexpr (MINB > 0) {
+    e = cudaFuncSetAttribute(apply3d_f32r_kernel_mb<P, S1, S2, S3, false, PD, BF, MINB>, a, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel_mb<P, S1, S2, S3, true, PD, BF, MINB>, a, sk);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched_mb<P, S1, S2, S3, false, PD, BF, MINB>, a, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched_mb<P, S1, S2, S3, true, PD, BF, MINB>, a, sk);
+  } else {
+    e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, false, PD, BF>, a, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, true, PD, BF>, a, sk);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF>, a, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF>, a, sk);
+  }
   return e;
 }
 
-// BF = true: the same kernel reading bfloat16-stored factors.
-template <int P, int S1, int S2, int S3, bool BF = false, int PD = IGASF_F32R_PD>
+// BF: bfloat16-stored factors. PD: slabs prefetched ahead. MINB: minimum
+// resident blocks per SM asked of the register allocator (0: its own choice).
+template <int P, int S1, int S2, int S3, bool BF = false, int PD = 2, int MINB = 0>
 ApplyKernel make_apply3d_f32r() {
   using G = TileF2R<P, S1, S2, S3>;
   static_assert(G::NT <= 1024, "tile too large for one block");
@@ -435,11 +452,11 @@ ApplyKernel make_apply3d_f32r() {
   k.plane = G::PL;
   k.lanes = 2;
   k.variant = IGASF_KERNEL_REGISTERS;
-  k.launch[IGASF_MASS] = &launch_apply3d_f32r<P, S1, S2, S3, false, PD, BF>;
-  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32r<P, S1, S2, S3, true, PD, BF>;
-  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF>;
-  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF>;
-  k.prepare = &prepare_apply3d_f32r<P, S1, S2, S3, PD, BF>;
+  k.launch[IGASF_MASS] = &launch_apply3d_f32r<P, S1, S2, S3, false, PD, BF, MINB>;
+  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32r<P, S1, S2, S3, true, PD, BF, MINB>;
+  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF, MINB>;
+  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF, MINB>;
+  k.prepare = &prepare_apply3d_f32r<P, S1, S2, S3, PD, BF, MINB>;
   return k;
 }
 
