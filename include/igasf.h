@@ -97,15 +97,28 @@ typedef struct {
   int tile[3];           /* elements per tile per direction, 0 = the library's choice;
                             honoured only where a kernel is built for that shape */
   int kernel_variant;    /* IGASF_KERNEL_*, 0 = the library's choice */
-  int reserved[7];       /* must be zero */
+  int geometry;          /* IGASF_GEOMETRY_*, 0 = stored factors */
+  int reserved[6];       /* must be zero */
 } igasf_options;
+
+/* Where the FP32 apply gets the factors w F.
+ * STORED: computed once at setup (FP64, Sec. 6.2) and streamed from HBM.
+ * ON_THE_FLY: the FP32 3D tile kernel evaluates them itself at every apply
+ *   from the control points (Sec. 6.2: G and its derivatives by the same
+ *   sum factorization as u, then det J, the cofactors of J and the
+ *   coefficient at G(x)), in FP32; no FP32 factors are stored and the apply
+ *   reads O(N) bytes instead of O(p^3 N). Requires d = 3, FP32 among the
+ *   stored precisions and a constant or exp-sin-cos coefficient. FP64 and
+ *   BF16 stay stored. */
+enum { IGASF_GEOMETRY_STORED = 0, IGASF_GEOMETRY_ON_THE_FLY = 1 };
 
 /* How the FP32 and BF16 3D tile kernels receive their factors (FP64 and 2D
  * kernels have one scheme: per-thread loads). */
 enum {
   IGASF_KERNEL_DEFAULT = 0,
   IGASF_KERNEL_REGISTERS = 1, /* each thread loads its factors into registers, slabs ahead */
-  IGASF_KERNEL_RING = 2       /* bulk copies into a shared-memory ring by a producer warp */
+  IGASF_KERNEL_RING = 2,      /* bulk copies into a shared-memory ring by a producer warp */
+  IGASF_KERNEL_ON_THE_FLY = 3 /* reported by igasf_describe for IGASF_GEOMETRY_ON_THE_FLY */
 };
 
 typedef struct igasf_plan *igasf_handle;

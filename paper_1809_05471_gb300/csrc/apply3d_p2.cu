@@ -6,8 +6,10 @@
 //   register prefetch, tile 8, 8, 4
 //   TMA ring, tile 16, 8, 4
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
+// Factors evaluated on the fly (FP32): tile 8, 8, 2 first, then 8, 4, 4.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
+#include "apply3d_f32g.cuh"
 #include "apply3d_f32r.cuh"
 
 namespace igasf {
@@ -37,6 +39,13 @@ int apply3d_p2(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<2, 8, 8, 8, true>() : make_apply3d_f32<2, 8, 8, 8>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<2, 16, 8, 2, true>() : make_apply3d_f32<2, 16, 8, 2>();
 #endif
+  return n;
+}
+
+int apply3d_p2_geo(ApplyKernel *out, int max_out) {
+  int n = 0;
+  if (n < max_out) out[n++] = make_apply3d_f32g<2, 8, 8, 2, true>();
+  if (n < max_out) out[n++] = make_apply3d_f32g<2, 8, 4, 4, true>();
   return n;
 }
 

@@ -6,8 +6,10 @@
 //   TMA ring, tile 8, 4, 2
 //   TMA ring, tile 4, 4, 4
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
+// Factors evaluated on the fly (FP32): tile 4, 4, 2 first, then 4, 4, 4.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
+#include "apply3d_f32g.cuh"
 #include "apply3d_f32r.cuh"
 
 namespace igasf {
@@ -37,6 +39,13 @@ int apply3d_p4(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 2, 2, 4, true>() : make_apply3d_f32<4, 2, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 4, 4, 2, true>() : make_apply3d_f32<4, 4, 4, 2>();
 #endif
+  return n;
+}
+
+int apply3d_p4_geo(ApplyKernel *out, int max_out) {
+  int n = 0;
+  if (n < max_out) out[n++] = make_apply3d_f32g<4, 4, 4, 2, true>();
+  if (n < max_out) out[n++] = make_apply3d_f32g<4, 4, 4, 4, true>();
   return n;
 }
 

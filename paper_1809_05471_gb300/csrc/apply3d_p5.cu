@@ -6,8 +6,10 @@
 //   register prefetch, tile 4, 4, 4
 //   register prefetch, tile 4, 2, 4
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
+// Factors evaluated on the fly (FP32): tile 4, 2, 2 first, then 2, 2, 2.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
+#include "apply3d_f32g.cuh"
 #include "apply3d_f32r.cuh"
 
 namespace igasf {
@@ -37,6 +39,13 @@ int apply3d_p5(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<5, 2, 2, 2, true>() : make_apply3d_f32<5, 2, 2, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<5, 4, 2, 2, true>() : make_apply3d_f32<5, 4, 2, 2>();
 #endif
+  return n;
+}
+
+int apply3d_p5_geo(ApplyKernel *out, int max_out) {
+  int n = 0;
+  if (n < max_out) out[n++] = make_apply3d_f32g<5, 4, 2, 2, true>();
+  if (n < max_out) out[n++] = make_apply3d_f32g<5, 2, 2, 2, true>();
   return n;
 }
 

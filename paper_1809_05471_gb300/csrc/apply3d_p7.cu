@@ -6,8 +6,10 @@
 //   register prefetch, tile 2, 2, 4
 //   register prefetch, tile 4, 2, 2
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
+// Factors evaluated on the fly (FP32): tile 2, 2, 2 first, then 2, 2, 1.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
+#include "apply3d_f32g.cuh"
 #include "apply3d_f32r.cuh"
 
 namespace igasf {
@@ -35,6 +37,13 @@ int apply3d_p7(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 4, 2, 1, true>() : make_apply3d_f32<7, 4, 2, 1>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 2, true>() : make_apply3d_f32<7, 2, 2, 2>();
 #endif
+  return n;
+}
+
+int apply3d_p7_geo(ApplyKernel *out, int max_out) {
+  int n = 0;
+  if (n < max_out) out[n++] = make_apply3d_f32g<7, 2, 2, 2, false>();
+  if (n < max_out) out[n++] = make_apply3d_f32g<7, 2, 2, 1, false>();
   return n;
 }
 

@@ -6,8 +6,10 @@
 //   TMA ring, tile 2, 2, 2
 //   register prefetch, tile 2, 1, 2
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
+// Factors evaluated on the fly (FP32): tile 2, 2, 2 first, then 2, 2, 1.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
+#include "apply3d_f32g.cuh"
 #include "apply3d_f32r.cuh"
 
 namespace igasf {
@@ -33,6 +35,13 @@ int apply3d_p9(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<9, 2, 2, 1, true>() : make_apply3d_f32<9, 2, 2, 1>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<9, 2, 1, 1, true>() : make_apply3d_f32<9, 2, 1, 1>();
 #endif
+  return n;
+}
+
+int apply3d_p9_geo(ApplyKernel *out, int max_out) {
+  int n = 0;
+  if (n < max_out) out[n++] = make_apply3d_f32g<9, 2, 2, 2, false>();
+  if (n < max_out) out[n++] = make_apply3d_f32g<9, 2, 2, 1, false>();
   return n;
 }
 

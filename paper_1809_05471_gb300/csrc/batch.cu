@@ -204,20 +204,7 @@ int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, 
     auto &G = b->groups[gi];
     G.patches.push_back(i);
     ApplyParams prm;
-    memset(&prm, 0, sizeof(prm));
-    prm.vpart = v.vpart;
-    prm.D = op == IGASF_MASS ? v.L.DM : v.L.DK;
-    for (int a = 0; a < kMaxDim; ++a) {
-      prm.tabB[a] = v.tabB[a];
-      prm.tabD[a] = v.tabD[a];
-      prm.N[a] = h->N[a];
-      prm.K[a] = h->K[a];
-      prm.T[a] = v.T[a];
-      prm.Qpad[a] = v.Qpad[a];
-    }
-    prm.ntiles = v.ntiles;
-    prm.status = h->status;
-    prm.wait_limit = h->wait_limit;
+    make_apply_params(h, v, op, nullptr, v.vpart, &prm);
     prm.skip_slab = -1;
     G.h_params.push_back(prm);
     GatherParams &gp = b->h_gp[i];

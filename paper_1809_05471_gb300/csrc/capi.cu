@@ -61,7 +61,9 @@ void free_plan(igasf_plan *h) {
     for (int a = 0; a < kMaxDim; ++a) {
       cudaFree(v.tabB[a]);
       cudaFree(v.tabD[a]);
+      cudaFree(v.wq32[a]);
     }
+    cudaFree(v.ctrl32);
     cudaFree(v.vpart);
     cudaFree(v.u_stage);
     cudaFree(v.v_stage);
@@ -137,6 +139,30 @@ namespace igasf {
 // scratch buffer in place of the plan's workspace.
 int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
+void make_apply_params(const igasf_plan *h, const Variant &var, int op, const void *u, void *vpart,
+                       ApplyParams *prm) {
+  memset(prm, 0, sizeof(*prm));
+  prm->u = u;
+  prm->vpart = vpart;
+  prm->D = op == IGASF_MASS ? var.L.DM : var.L.DK;
+  for (int a = 0; a < kMaxDim; ++a) {
+    prm->tabB[a] = var.tabB[a];
+    prm->tabD[a] = var.tabD[a];
+    prm->N[a] = h->N[a];
+    prm->K[a] = h->K[a];
+    prm->T[a] = var.T[a];
+    prm->Qpad[a] = var.Qpad[a];
+    prm->wq[a] = var.wq32[a];
+  }
+  prm->ntiles = var.ntiles;
+  prm->status = h->status;
+  prm->wait_limit = h->wait_limit;
+  prm->skip_slab = h->skip_slab;
+  prm->ctrl = var.ctrl32;
+  prm->coef_kind = h->coef_kind;
+  prm->coef_a = (float)(h->coef_kind == IGASF_COEF_EXP_SIN_COS ? h->coef_alpha : h->coef_constant);
+}
+
 int apply_with_workspace(igasf_plan *h, int op, int prec, const void *u, void *v, void *ws,
                          size_t ws_bytes, void *stream) {
   if (!h) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL");
@@ -156,22 +182,7 @@ int apply_with_workspace(igasf_plan *h, int op, int prec, const void *u, void *v
   if (ub < vb + len && vb < ub + len) return fail(IGASF_ERR_INVALID_ARG, "u and v overlap");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ApplyParams prm;
-  memset(&prm, 0, sizeof(prm));
-  prm.u = u;
-  prm.vpart = ws;
-  prm.D = op == IGASF_MASS ? var.L.DM : var.L.DK;
-  for (int a = 0; a < kMaxDim; ++a) {
-    prm.tabB[a] = var.tabB[a];
-    prm.tabD[a] = var.tabD[a];
-    prm.N[a] = h->N[a];
-    prm.K[a] = h->K[a];
-    prm.T[a] = var.T[a];
-    prm.Qpad[a] = var.Qpad[a];
-  }
-  prm.ntiles = var.ntiles;
-  prm.status = h->status;
-  prm.wait_limit = h->wait_limit;
-  prm.skip_slab = h->skip_slab;
+  make_apply_params(h, var, op, u, ws, &prm);
   cudaError_t e = var.k.launch[op](prm, s);
   if (e != cudaSuccess) return cuda_fail(e, "apply kernel launch");
   e = launch_gather(h->d, vectors_are_float(prec), ws, v, h->N, var.T, var.k.S, h->p, s);
@@ -216,6 +227,11 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     return fail(IGASF_ERR_INVALID_ARG, "options.precisions has unknown bits 0x%x", precs);
   if (!(precs & IGASF_PREC_BIT(o.default_prec)))
     return fail(IGASF_ERR_INVALID_ARG, "options.precisions must include default_prec");
+  if (o.geometry != IGASF_GEOMETRY_STORED && o.geometry != IGASF_GEOMETRY_ON_THE_FLY)
+    return fail(IGASF_ERR_INVALID_ARG, "options.geometry = %d", o.geometry);
+  const bool geo = o.geometry == IGASF_GEOMETRY_ON_THE_FLY;
+  if (geo && !(precs & IGASF_PREC_BIT(IGASF_FP32)))
+    return fail(IGASF_ERR_INVALID_ARG, "factors on the fly are an FP32 mode: store FP32");
   igasf_coef c;
   c.kind = IGASF_COEF_CONSTANT;
   c.constant = 1.0;
@@ -236,10 +252,19 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
   }
   if (ntot >= 2147483647.0 || qtot >= 9.0e15)
     return fail(IGASF_ERR_UNSUPPORTED, "patch too large: %.0f dofs (limit 2^31 - 1)", ntot);
+  if (geo && d != 3) return fail(IGASF_ERR_UNSUPPORTED, "factors on the fly are built for d = 3");
+  if (geo && c.kind == IGASF_COEF_VALUES)
+    return fail(IGASF_ERR_UNSUPPORTED, "factors on the fly need a constant or exp-sin-cos coefficient");
   // which kernels
   ApplyKernel kern[kNumPrec];
   for (int prec = 0; prec < kNumPrec; ++prec) {
     if (!(precs & IGASF_PREC_BIT(prec))) continue;
+    if (geo && prec == IGASF_FP32) {
+      if (!find_geometry_kernel(p, o.tile, &kern[prec]))
+        return fail(IGASF_ERR_UNSUPPORTED, "tile (%d, %d, %d) is not built for factors on the fly at p=%d",
+                    o.tile[0], o.tile[1], o.tile[2], p);
+      continue;
+    }
     if (!find_apply_kernel(d, p, prec, nullptr, 0, &kern[prec]))
       return fail(IGASF_ERR_UNSUPPORTED, "no kernel for d=%d p=%d prec=%d", d, p, prec);
     if (!find_apply_kernel(d, p, prec, o.tile, o.kernel_variant, &kern[prec]))
@@ -253,6 +278,9 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
   h->d = d;
   h->p = p;
   h->default_prec = o.default_prec;
+  h->coef_kind = c.kind;
+  h->coef_constant = c.constant;
+  h->coef_alpha = c.alpha;
   TRY_CUDA(cudaGetDevice(&h->device), "cudaGetDevice");
   TRY(alloc((void **)&h->status, sizeof(unsigned int), "status word"));
   TRY_CUDA(cudaMemset(h->status, 0, sizeof(unsigned int)), "status word");
@@ -310,14 +338,33 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     v.L.plane = v.k.plane;
     v.L.lanes = v.k.lanes;
     v.L.elem_bytes = factor_bytes(prec);
+    v.on_the_fly = geo && prec == IGASF_FP32;
     const int64_t Qlast = (int64_t)v.k.S[d - 1] * p;
     const int64_t rows = (int64_t)v.ntiles * Qlast;
-    v.bytesM = (size_t)rows * 1 * v.L.plane * v.L.elem_bytes;
-    v.bytesK = (size_t)rows * num_fields(d, IGASF_STIFFNESS) * v.L.plane * v.L.elem_bytes;
-    TRY(alloc(&v.L.DM, v.bytesM, "mass factors"));
-    TRY(alloc(&v.L.DK, v.bytesK, "stiffness factors"));
-    TRY_CUDA(cudaMemsetAsync(v.L.DM, 0, v.bytesM, s), "memset");
-    TRY_CUDA(cudaMemsetAsync(v.L.DK, 0, v.bytesK, s), "memset");
+    if (!v.on_the_fly) {
+      v.bytesM = (size_t)rows * 1 * v.L.plane * v.L.elem_bytes;
+      v.bytesK = (size_t)rows * num_fields(d, IGASF_STIFFNESS) * v.L.plane * v.L.elem_bytes;
+      TRY(alloc(&v.L.DM, v.bytesM, "mass factors"));
+      TRY(alloc(&v.L.DK, v.bytesK, "stiffness factors"));
+      TRY_CUDA(cudaMemsetAsync(v.L.DM, 0, v.bytesM, s), "memset");
+      TRY_CUDA(cudaMemsetAsync(v.L.DK, 0, v.bytesK, s), "memset");
+    } else {
+      // control points (FP32, one array per component) and padded FP32 weights
+      std::vector<float> cs((size_t)3 * h->Ntot);
+      for (int64_t n = 0; n < h->Ntot; ++n)
+        for (int i = 0; i < 3; ++i) cs[(size_t)i * h->Ntot + n] = (float)ctrl[n * 3 + i];
+      TRY(alloc((void **)&v.ctrl32, sizeof(float) * cs.size(), "control points"));
+      TRY_CUDA(cudaMemcpy(v.ctrl32, cs.data(), sizeof(float) * cs.size(), cudaMemcpyHostToDevice), "copy");
+      for (int a = 0; a < d; ++a) {
+        std::vector<double> wd(h->Q[a]);
+        std::vector<float> wf(v.Qpad[a], 0.f);
+        TRY_CUDA(cudaMemcpy(wd.data(), h->weights[a], sizeof(double) * h->Q[a], cudaMemcpyDeviceToHost),
+                 "weights");
+        for (int q = 0; q < h->Q[a]; ++q) wf[q] = (float)wd[q];
+        TRY(alloc((void **)&v.wq32[a], sizeof(float) * v.Qpad[a], "weights"));
+        TRY_CUDA(cudaMemcpy(v.wq32[a], wf.data(), sizeof(float) * v.Qpad[a], cudaMemcpyHostToDevice), "copy");
+      }
+    }
     for (int a = 0; a < d; ++a) {
       TRY(alloc(&v.tabB[a], es * p * v.Qpad[a], "tables"));
       TRY(alloc(&v.tabD[a], es * p * v.Qpad[a], "tables"));
@@ -331,7 +378,7 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     TRY(alloc(&v.u_stage, (size_t)h->Ntot * es, "staging"));
     TRY(alloc(&v.v_stage, (size_t)h->Ntot * es, "staging"));
     TRY_CUDA(v.k.prepare(), "kernel attributes");
-    g.out[g.nout++] = v.L;
+    if (!v.on_the_fly) g.out[g.nout++] = v.L;
   }
   // geometry factors
   double *ctrl_d = nullptr, *coef_d = nullptr;
@@ -402,22 +449,7 @@ int igasf_apply_prec(igasf_handle h, int op, int prec, const void *u, void *v, v
   if (ub < vb + len && vb < ub + len) return fail(IGASF_ERR_INVALID_ARG, "u and v overlap");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ApplyParams prm;
-  memset(&prm, 0, sizeof(prm));
-  prm.u = u;
-  prm.vpart = var.vpart;
-  prm.D = op == IGASF_MASS ? var.L.DM : var.L.DK;
-  for (int a = 0; a < kMaxDim; ++a) {
-    prm.tabB[a] = var.tabB[a];
-    prm.tabD[a] = var.tabD[a];
-    prm.N[a] = h->N[a];
-    prm.K[a] = h->K[a];
-    prm.T[a] = var.T[a];
-    prm.Qpad[a] = var.Qpad[a];
-  }
-  prm.ntiles = var.ntiles;
-  prm.status = h->status;
-  prm.wait_limit = h->wait_limit;
-  prm.skip_slab = h->skip_slab;
+  make_apply_params(h, var, op, u, var.vpart, &prm);
   cudaEvent_t *ev = nullptr;
   if ((size_t)(h->prof_next + 1) * 3 <= h->prof_events.size()) {
     ev = &h->prof_events[(size_t)h->prof_next * 3];
@@ -585,6 +617,8 @@ int igasf_get_factors(igasf_handle h, int op, int prec, double *out) {
   if (op != IGASF_MASS && op != IGASF_STIFFNESS) return fail(IGASF_ERR_INVALID_ARG, "op = %d", op);
   if (prec < 0 || prec >= kNumPrec || !h->var[prec].present)
     return fail(IGASF_ERR_UNSUPPORTED, "precision %d was not stored at setup", prec);
+  if (h->var[prec].on_the_fly)
+    return fail(IGASF_ERR_UNSUPPORTED, "precision %d evaluates its factors on the fly: none are stored", prec);
   const int nf = num_fields(h->d, op);
   const size_t bytes = sizeof(double) * (size_t)h->Qtot * nf;
   double *tmp = nullptr;

@@ -38,6 +38,12 @@ struct ApplyParams {
   unsigned int *status;       // device word: bit 0 set when a bounded wait ran out
   long long wait_limit;       // clock cycles a kernel may wait on one mbarrier phase
   int skip_slab;              // test hook: tile 0 never fills this factor slab (-1: off)
+  // factors evaluated on the fly (D unused): control points SoA [3][N],
+  // Gauss weights per direction padded like the tables, coefficient
+  const float *ctrl;
+  const float *wq[kMaxDim];
+  int coef_kind;              // IGASF_COEF_CONSTANT or IGASF_COEF_EXP_SIN_COS
+  float coef_a;               // the constant, or alpha
 };
 
 // Many patches' tiles in one launch (device arrays): params[patch], and for
@@ -70,6 +76,9 @@ int list_apply_kernels(int d, int p, int prec, ApplyKernel *out, int max_out);
 // tile matches every non-zero entry of `tile` and whose variant matches a
 // non-zero `variant`; false if none is built.
 bool find_apply_kernel(int d, int p, int prec, const int *tile, int variant, ApplyKernel *out);
+// FP32 3D kernels that evaluate the factors on the fly (default first).
+int list_geometry_kernels(int p, ApplyKernel *out, int max_out);
+bool find_geometry_kernel(int p, const int *tile, ApplyKernel *out);
 
 // Tile-major layout of the factors (see layout.h for the exact order).
 struct FactorLayout {

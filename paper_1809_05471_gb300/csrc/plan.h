@@ -23,6 +23,10 @@ struct Variant {
   void *vpart = nullptr;
   size_t vpart_bytes = 0;
   void *u_stage = nullptr, *v_stage = nullptr;
+  // factors evaluated on the fly (FP32 only): no stored factors
+  bool on_the_fly = false;
+  float *ctrl32 = nullptr;                            // SoA [3][N]
+  float *wq32[kMaxDim] = {nullptr, nullptr, nullptr}; // [Qpad]
 };
 
 }  // namespace igasf
@@ -46,4 +50,12 @@ struct igasf_plan {
   int prof_next = 0;                     // applies recorded so far
   double *dinv64 = nullptr;              // inverse Jacobi diagonal of K (solver), lazily
   float *dinv32 = nullptr;
+  int coef_kind = IGASF_COEF_CONSTANT;   // for factors evaluated on the fly
+  double coef_constant = 1.0, coef_alpha = 0.0;
 };
+
+namespace igasf {
+// Arguments of one tile-kernel launch of the plan's precision `var` (capi.cu).
+void make_apply_params(const igasf_plan *h, const Variant &var, int op, const void *u, void *vpart,
+                       ApplyParams *prm);
+}  // namespace igasf

@@ -27,6 +27,9 @@ COEF_VALUES = 2
 KERNEL_DEFAULT = 0
 KERNEL_REGISTERS = 1
 KERNEL_RING = 2
+KERNEL_ON_THE_FLY = 3
+GEOMETRY_STORED = 0
+GEOMETRY_ON_THE_FLY = 1     # FP32 applies evaluate the factors inside the tile kernel
 
 ERRORS = {
     -1: "INVALID_ARG", -2: "KNOTS", -3: "GEOMETRY", -4: "UNSUPPORTED", -5: "CUDA",
@@ -59,7 +62,7 @@ class Coef(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precisions", ctypes.c_uint), ("default_prec", ctypes.c_int),
                 ("tile", ctypes.c_int * 3), ("kernel_variant", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("geometry", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class CgReport(ctypes.Structure):
@@ -154,7 +157,8 @@ class Plan:
                  ctrl: np.ndarray, coef_kind: int = COEF_CONSTANT, coef_constant: float = 1.0,
                  coef_alpha: float = 0.0, coef_values: Optional[np.ndarray] = None,
                  precisions: Sequence[int] = (FP64,), default_prec: Optional[int] = None,
-                 tile: Optional[Sequence[int]] = None, kernel_variant: int = 0):
+                 tile: Optional[Sequence[int]] = None, kernel_variant: int = 0,
+                 geometry: int = GEOMETRY_STORED):
         lib = load_library()
         self.d = d
         self._orders = (ctypes.c_int * d)(*orders)
@@ -176,6 +180,7 @@ class Plan:
             for i, s in enumerate(tile):
                 opt.tile[i] = int(s)
         opt.kernel_variant = int(kernel_variant)
+        opt.geometry = int(geometry)
         h = ctypes.c_void_p()
         _check(lib.igasf_setup(d, self._orders, self._lens, self._kptrs, _dptr(self._ctrl),
                                ctypes.byref(coef), ctypes.byref(opt), ctypes.byref(h)))

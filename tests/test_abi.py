@@ -135,6 +135,30 @@ def test_rejects_null_and_bad_options(lib):
     assert rc == -1
 
 
+def test_rejects_bad_geometry_options(lib):
+    """Factors on the fly: a known mode, FP32 stored, d = 3, and a coefficient
+    the kernel can evaluate; all checked on the host before any device work."""
+    pt = _patch()
+    opt = G.Options()
+    opt.geometry = 5
+    rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, opt=opt)
+    assert rc == -1
+    opt = G.Options()
+    opt.geometry = G.GEOMETRY_ON_THE_FLY            # default precisions: FP64 only
+    rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, opt=opt)
+    assert rc == -1
+    assert b"FP32" in lib.igasf_last_error_message()
+    opt.precisions = 1 << G.FP32
+    opt.default_prec = G.FP32
+    vals = np.ones(8)
+    coef = G.Coef(G.COEF_VALUES, 0.0, 0.0, vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, coef=coef, opt=opt)
+    assert rc == -4
+    p2, _ = I.make_patch(2, 3, 4, seed=0)
+    rc, _ = _setup(lib, 2, [3] * 2, p2.knots, p2.ctrl, opt=opt)
+    assert rc == -4
+
+
 def test_null_handle_calls(lib):
     assert lib.igasf_apply(None, 0, None, None, None) == -1
     assert lib.igasf_apply_prec(None, 0, 0, None, None, None) == -1
