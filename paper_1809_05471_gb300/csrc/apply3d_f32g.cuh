@@ -82,8 +82,9 @@ __device__ __forceinline__ void apply3d_f32g_body(const ApplyParams &prm, const 
   const int e01 = t1 * S1, e02 = t2 * S2, e03 = t3 * S3;
   const int ke3 = min(S3, prm.K[2] - e03);
 
-  // ---- stage tables, u, control points and weights
-  stage_tile_f32<P, S1, S2, S3, NT, STIFF>(prm, tid, e01, e02, e03, t1b, t1d, t2b, t2d, t3b, t3d, us);
+  // ---- stage tables (the derivative tables too: the geometry needs them for
+  // the mass as well), u, control points and weights
+  stage_tile_f32<P, S1, S2, S3, NT, true>(prm, tid, e01, e02, e03, t1b, t1d, t2b, t2d, t3b, t3d, us);
   {
     constexpr int AC = (3 * VOL + NT - 1) / NT, AW = (Q1 + Q2 + Q3 + NT - 1) / NT;
     const int N1 = prm.N[0], N2 = prm.N[1], N3 = prm.N[2];
