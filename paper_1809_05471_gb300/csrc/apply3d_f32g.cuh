@@ -303,11 +303,20 @@ __device__ __forceinline__ void apply3d_f32g_body(const ApplyParams &prm, const 
             const float2 C22 = cof(J[0][0], J[0][1], J[1][0], J[1][1]);
             float2 a = make_float2(prm.coef_a, prm.coef_a);
             if (coef_var) {
-              a.x = __expf(prm.coef_a * sinpif(2.f * Gv[0].x) * cospif(2.f * Gv[1].x));
-              a.y = __expf(prm.coef_a * sinpif(2.f * Gv[0].y) * cospif(2.f * Gv[1].y));
+              // fast hardware sine, cosine and exponential; the period is taken
+              // out exactly first (x - rint(x) in [-1/2, 1/2]), so the sine and
+              // cosine see arguments in [-pi, pi], where their absolute error
+              // (~1e-6) is far inside the FP32 tolerance
+              constexpr float twopi = 6.28318530717958647692f;
+              const float sx = __sinf(twopi * (Gv[0].x - rintf(Gv[0].x)));
+              const float sy = __sinf(twopi * (Gv[0].y - rintf(Gv[0].y)));
+              const float cx = __cosf(twopi * (Gv[1].x - rintf(Gv[1].x)));
+              const float cy = __cosf(twopi * (Gv[1].y - rintf(Gv[1].y)));
+              a.x = __expf(prm.coef_a * sx * cx);
+              a.y = __expf(prm.coef_a * sy * cy);
             }
-            const float2 s = make_float2(w.x > 0.f ? w.x * a.x / fabsf(det.x) : 0.f,
-                                         w.y > 0.f ? w.y * a.y / fabsf(det.y) : 0.f);
+            const float2 s = make_float2(w.x > 0.f ? __fdividef(w.x * a.x, fabsf(det.x)) : 0.f,
+                                         w.y > 0.f ? __fdividef(w.y * a.y, fabsf(det.y)) : 0.f);
             const float2 D11 = fmul2(s, ffma2(C20, C20, ffma2(C10, C10, fmul2(C00, C00))));
             const float2 D12 = fmul2(s, ffma2(C20, C21, ffma2(C10, C11, fmul2(C00, C01))));
             const float2 D13 = fmul2(s, ffma2(C20, C22, ffma2(C10, C12, fmul2(C00, C02))));
