@@ -101,9 +101,19 @@ def apply_flops(op, p, K, d=3):
     return 2 * fwd + 15 * Q1 ** 3
 
 
+def sources_digest(names):
+    """First 16 hex digits of the SHA-256 of the named kernel sources, concatenated."""
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1809_05471_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(kernel_key):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current source of that kernel; else None."""
+    current sources of that kernel (the kernel template, what it includes, and
+    the file that instantiates the default candidate); else None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
@@ -113,12 +123,11 @@ def traffic_record(kernel_key):
     ent = rec.get(kernel_key)
     if not ent:
         return None
-    src = os.path.join(ROOT, "paper_1809_05471_gb300", "csrc", ent.get("source", ""))
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = sources_digest(ent.get("sources", []))
     except OSError:
         return None
-    if ent.get("source_sha256_16") != h:
+    if ent.get("sources_sha256_16") != h:
         return None
     return ent.get("dram_bytes_per_launch")
 
