@@ -219,7 +219,9 @@ struct TileF2 {
   static_assert(Q1 % 2 == 0, "pencil pairs need an even number of q1 points per tile");
   static constexpr int H1 = Q1 / 2;                 // pencil pairs per q1 row
   static constexpr int NPEN = Q1 * Q2;
-  static constexpr int PL = (NPEN + 31) / 32 * 32;  // plane (pencils), layout row length
+  // plane (pencils), the layout row length: padded to a multiple of 8 so that
+  // every slab is a whole number of 16-byte units in each storage format
+  static constexpr int PL = (NPEN + 7) / 8 * 8;
   static constexpr int UNITS = PL / 2;              // pairs per layout row
   static constexpr int NPAIR = H1 * Q2;
   static constexpr int NTC = (NPAIR + 31) / 32 * 32;  // consumer threads

@@ -51,6 +51,10 @@ struct AsmDims {
   const double *tabB[3], *tabD[3];  // FP64 [j][Q_a]
   int stiff;                  // 0: mass, 1: stiffness
   int nterms, ngroups, nf;
+  // products of the two univariate tables over the shared elements of every pair:
+  // PT[a][choice][m][o][i][k] = tm(m - e, q) tn(n - e, q), e = first shared
+  // element + i, q = e p + k; choice = 2 (psi differentiated) + (phi differentiated)
+  const double *PT[3];
 };
 
 // term t of the stiffness form: (i, j) = (t / d, t % d)
@@ -84,22 +88,53 @@ __device__ __forceinline__ void common_elements(const AsmDims &g, int a, int m, 
   hi = min(min(m, n), min(ehi, g.K[a] - 1));
 }
 
-// sum over the shared quadrature points of direction a of psi_m phi_n x(q)
-// (tables chosen by dm, dn), x read at x_base + (q - q0) * x_stride
-__device__ __forceinline__ double contract(const AsmDims &g, int a, bool dm, bool dn, int m, int n,
+// sum over the shared quadrature points of direction a, elements lo..hi (a
+// sub-range of the pair's shared elements), of psi_m phi_n x(q), with the
+// products psi_m phi_n read from the pair-product table (one FMA per point);
+// x read at x + (q - q0) * x_stride
+__device__ __forceinline__ double contract(const AsmDims &g, int a, bool dm, bool dn, int m, int o,
                                            int lo, int hi, const double *x, int64_t x_stride,
                                            int q0) {
-  const int p = g.p, Q = g.Q[a];
-  const double *tm = dm ? g.tabD[a] : g.tabB[a];
-  const double *tn = dn ? g.tabD[a] : g.tabB[a];
+  const int p = g.p, n = m + o - (p - 1);
+  const int first = max(max(m, n) - (p - 1), 0);
+  const int choice = 2 * dm + dn;
+  const double *pt = g.PT[a] + ((((int64_t)choice * g.N[a] + m) * g.W + o) * p) * p;
   double s = 0.0;
   for (int e = lo; e <= hi; ++e) {
-    const double *am = tm + (int64_t)(m - e) * Q + e * p;
-    const double *an = tn + (int64_t)(n - e) * Q + e * p;
+    const double *pe = pt + (e - first) * p;
     const double *xe = x + (int64_t)(e * p - q0) * x_stride;
-    for (int k = 0; k < p; ++k) s += am[k] * an[k] * xe[k * x_stride];
+    for (int k = 0; k < p; ++k) s = fma(pe[k], xe[k * x_stride], s);
   }
   return s;
+}
+
+// pair-product tables of one direction: one thread per (choice, m, o, i, k)
+__global__ void pair_table_kernel(const AsmDims g, int a, double *PT) {
+  const int p = g.p, W = g.W, N = g.N[a];
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)4 * N * W * p * p) return;
+  const int k = (int)(idx % p);
+  int64_t r = idx / p;
+  const int i = (int)(r % p);
+  r /= p;
+  const int o = (int)(r % W);
+  r /= W;
+  const int m = (int)(r % N);
+  const int choice = (int)(r / N);
+  const int n = m + o - (p - 1);
+  double v = 0.0;
+  if (n >= 0 && n < N) {
+    const int first = max(max(m, n) - (p - 1), 0);
+    const int last = min(min(m, n), g.K[a] - 1);
+    const int e = first + i;
+    if (e <= last) {
+      const int Q = g.Q[a], q = e * p + k;
+      const double *tm = (choice & 2) ? g.tabD[a] : g.tabB[a];
+      const double *tn = (choice & 1) ? g.tabD[a] : g.tabB[a];
+      v = tm[(int64_t)(m - e) * Q + q] * tn[(int64_t)(n - e) * Q + q];
+    }
+  }
+  PT[idx] = v;
 }
 
 // ---- chunk factors, lexicographic: Fc[f][qc][qmid][q1] ------------------------
@@ -142,7 +177,7 @@ __global__ void level1_kernel(const AsmDims g, const double *Fc, int QC, int Qmi
     int lo, hi;
     common_elements(g, 0, m1, n1, 0, g.K[0] - 1, lo, hi);
     const double *x = Fc + (((int64_t)term_field(g, t) * QC + qc) * Qmid + qmid) * g.Q[0];
-    s = contract(g, 0, term_i(g, t) == 0, term_j(g, t) == 0, m1, n1, lo, hi, x, 1, 0);
+    s = contract(g, 0, term_i(g, t) == 0, term_j(g, t) == 0, m1, o1, lo, hi, x, 1, 0);
   }
   L1[idx] = s;
 }
@@ -168,7 +203,7 @@ __global__ void level2_kernel(const AsmDims g, const double *L1, int QC, double 
     for (int t = 0; t < g.nterms; ++t) {
       const double *x = L1 + ((int64_t)t * QC + qc) * Q2 * inner1 + e1;
       acc[term_group(g, t)] +=
-          contract(g, 1, term_i(g, t) == 1, term_j(g, t) == 1, m2, n2, lo, hi, x, inner1, 0);
+          contract(g, 1, term_i(g, t) == 1, term_j(g, t) == 1, m2, o2, lo, hi, x, inner1, 0);
     }
   }
   const int64_t off = (int64_t)qc * inner + ((int64_t)m2 * W + o2) * inner1 + e1;
@@ -275,7 +310,7 @@ __global__ void last_level_kernel(const AsmDims g, const CsrDims c, const double
   double s = 0.0;
   for (int gg = 0; gg < g.ngroups; ++gg) {
     const double *x = Lprev + (int64_t)gg * QC * inner + e_in;
-    s += contract(g, a, (gg & 2) != 0 && g.stiff, (gg & 1) != 0 && g.stiff, m[a], nL, lo, hi, x,
+    s += contract(g, a, (gg & 2) != 0 && g.stiff, (gg & 1) != 0 && g.stiff, m[a], o[a], lo, hi, x,
                   inner, e0 * p);
   }
   values[row_start(g, c, m) + rank_in_row(g, m, o)] += s;
@@ -348,12 +383,19 @@ extern "C" int igasf_assemble_csr(igasf_handle h, int op, int64_t *rowptr, int64
   const int64_t QCmax = (int64_t)layers * p;
 
   int64_t *pre_d = nullptr;
-  double *Fc = nullptr, *L1 = nullptr, *L2 = nullptr;
+  double *Fc = nullptr, *L1 = nullptr, *L2 = nullptr, *PT = nullptr;
+  size_t pt_off[3] = {0, 0, 0}, pt_total = 0;
+  for (int a = 0; a < d; ++a) {
+    pt_off[a] = pt_total;
+    pt_total += (size_t)4 * g.N[a] * W * p * p;
+  }
   cudaError_t e = cudaMalloc((void **)&pre_d, sizeof(int64_t) * pre_h.size());
+  if (e == cudaSuccess) e = cudaMalloc((void **)&PT, sizeof(double) * pt_total);
   if (e == cudaSuccess) e = cudaMalloc((void **)&Fc, sizeof(double) * g.nf * QCmax * Qmid * g.Q[0]);
   if (e == cudaSuccess) e = cudaMalloc((void **)&L1, sizeof(double) * g.nterms * QCmax * Qmid * inner1);
   if (e == cudaSuccess && d == 3) e = cudaMalloc((void **)&L2, sizeof(double) * g.ngroups * QCmax * inner);
   auto release = [&]() {
+    cudaFree(PT);
     cudaFree(pre_d);
     cudaFree(Fc);
     cudaFree(L1);
@@ -374,6 +416,11 @@ extern "C" int igasf_assemble_csr(igasf_handle h, int op, int64_t *rowptr, int64
   }
   const int64_t nnz = igasf_assembled_nnz(h);
   const int T = 256;
+  for (int a = 0; a < d && e == cudaSuccess; ++a) {
+    g.PT[a] = PT + pt_off[a];
+    pair_table_kernel<<<blocks_for((int64_t)4 * g.N[a] * W * p * p, T), T, 0, s>>>(g, a, PT + pt_off[a]);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(values, 0, sizeof(double) * nnz, s);
   if (e == cudaSuccess) {
     csr_structure_kernel<<<blocks_for(Ntot * Wd, T), T, 0, s>>>(g, c, rowptr, colind);
