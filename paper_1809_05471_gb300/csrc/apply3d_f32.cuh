@@ -423,7 +423,7 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
             const int q3 = e3 * P + qq;
             const uint32_t g = gbase + q3, slot = g % R, parity = (g / R) & 1;
             if (!mbar_wait_bounded(smem_addr(&full[slot]), parity, prm.wait_limit)) bad = true;
-            float4 dc[NCH];
+            float4 dc[NCH] = {};
             float2 dm = make_float2(0.f, 0.f);
             if (has_pair) {
               const Chunk *rs = reinterpret_cast<const Chunk *>(ring + (size_t)slot * SB);

@@ -211,7 +211,7 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
         for (int qq = 0; qq < P; ++qq) {
           const int q3 = e3 * P + qq;
           // factors of this slab, then request slab q3 + PD into the freed slot
-          float4 dc[NCH];
+          float4 dc[NCH] = {};
           float2 dm = make_float2(0.f, 0.f);
           if constexpr (STIFF) {
 #pragma unroll
