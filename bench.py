@@ -575,7 +575,8 @@ def run_reference(args):
 
 def assembly_flops(d, p, K, op):
     """Floating-point operations of the sum-factorized assembly as implemented
-    (3 per inner term: two products and an add), counted from the loop bounds."""
+    (one FMA, 2 flop, per inner term: the product of the two univariate tables is
+    precomputed per pair), counted from the loop bounds."""
     W = 2 * p - 1
     N = K + p - 1
     # sum over (m, o) valid of (#shared elements) * p, one direction
@@ -594,7 +595,7 @@ def assembly_flops(d, p, K, op):
         it = nterms * Q * Q * C + nterms * Q * C * N * W + ngroups * C * nnz1 * nnz1
     else:
         it = nterms * Q * C + ngroups * C * nnz1
-    return 3 * it
+    return 2 * it
 
 
 def run_assemble(args):
