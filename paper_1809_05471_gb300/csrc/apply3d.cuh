@@ -275,6 +275,7 @@ __device__ __forceinline__ void apply3d_body(const ApplyParams &prm, const int t
 template <typename T, int P, int S1, int S2, int S3, bool STIFF>
 __global__ void __launch_bounds__(Tile3<P, S1, S2, S3>::NT)
 apply3d_kernel(const ApplyParams prm) {
+  pdl_allow_dependents();
   apply3d_body<T, P, S1, S2, S3, STIFF>(prm, blockIdx.x);
 }
 

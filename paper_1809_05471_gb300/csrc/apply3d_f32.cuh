@@ -585,6 +585,7 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
 template <int P, int S1, int S2, int S3, bool STIFF, bool BF>
 __global__ void __launch_bounds__(TileF2<P, S1, S2, S3>::NT)
 apply3d_f32_kernel(const ApplyParams prm) {
+  pdl_allow_dependents();
   apply3d_f32_body<P, S1, S2, S3, STIFF, BF>(prm, blockIdx.x, gridDim.x, prm.ntiles);
 }
 

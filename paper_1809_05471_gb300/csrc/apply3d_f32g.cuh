@@ -442,6 +442,7 @@ __device__ __forceinline__ void apply3d_f32g_body(const ApplyParams &prm, const 
 template <int P, int S1, int S2, int S3, bool STIFF, bool ZALL>
 __global__ void __launch_bounds__(TileF2G<P, S1, S2, S3, ZALL>::NT)
 apply3d_f32g_kernel(const ApplyParams prm) {
+  pdl_allow_dependents();
   apply3d_f32g_body<P, S1, S2, S3, STIFF, ZALL>(prm, blockIdx.x);
 }
 

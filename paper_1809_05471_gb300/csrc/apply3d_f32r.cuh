@@ -369,12 +369,14 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
 template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
 apply3d_f32r_kernel(const ApplyParams prm) {
+  pdl_allow_dependents();
   apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(prm, blockIdx.x);
 }
 
 template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int MINB>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT, MINB)
 apply3d_f32r_kernel_mb(const ApplyParams prm) {
+  pdl_allow_dependents();
   apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(prm, blockIdx.x);
 }
 

@@ -324,6 +324,7 @@ __device__ __forceinline__ void apply3d_f32s_body(const ApplyParams &prm, const 
 template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
 __global__ void __launch_bounds__(TileF2S<P, S1, S2, S3>::NT)
 apply3d_f32s_kernel(const ApplyParams prm) {
+  pdl_allow_dependents();
   apply3d_f32s_body<P, S1, S2, S3, STIFF, PD, BF>(prm, blockIdx.x);
 }
 

@@ -22,6 +22,17 @@ inline bool vectors_are_float(int prec) { return prec != IGASF_FP64; }
 inline size_t vector_bytes(int prec) { return prec == IGASF_FP64 ? 8 : 4; }
 inline int factor_bytes(int prec) { return prec == IGASF_FP64 ? 8 : (prec == IGASF_FP32 ? 4 : 2); }
 
+#ifdef __CUDACC__
+// Programmatic dependent launch: a tile kernel lets the gather that follows it
+// on the stream be scheduled once every tile block has started; the gather
+// waits for the tile kernel's completion (and its memory) before reading.
+// Both are no-ops when the launch carries no programmatic dependency.
+__device__ __forceinline__ void pdl_allow_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait_primary() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
 // Arguments of one apply launch; pointers are device addresses in the
 // precision of the kernel (float or double).
 struct ApplyParams {

@@ -383,6 +383,7 @@ template <typename T, bool TWO>
 __global__ void gather_kernel(const T *__restrict__ vpart, T *__restrict__ v, int N0, int N1,
                               int Ntot, int T0, int T1, int T2, int S0, int S1, int S2, int E0,
                               int E1, int E2, int vol) {
+  pdl_wait_primary();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= Ntot) return;
   const int i0 = n % N0, r = n / N0;
@@ -430,9 +431,20 @@ cudaError_t launch_gather(int d, int float_vectors, const void *vpart, void *v, 
   const int Ntot = N[0] * N1 * N2;
   const bool two = E0 <= 2 * S[0] && E1 <= 2 * S1 && E2 <= 2 * S2;
   const int blocks = (Ntot + 255) / 256;
-#define IGASF_GATHER(TT, TWO_)                                                                 \
-  gather_kernel<TT, TWO_><<<blocks, 256, 0, s>>>((const TT *)vpart, (TT *)v, N[0], N1, Ntot, T[0], \
-                                                 T1, T2, S[0], S1, S2, E0, E1, E2, vol)
+  // launched with a programmatic dependency on the tile kernel before it
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+#define IGASF_GATHER(TT, TWO_)                                                                     \
+  return cudaLaunchKernelEx(&cfg, gather_kernel<TT, TWO_>, (const TT *)vpart, (TT *)v, N[0], N1, Ntot, \
+                            T[0], T1, T2, S[0], S1, S2, E0, E1, E2, vol)
   if (float_vectors) {
     if (two) IGASF_GATHER(float, true);
     else IGASF_GATHER(float, false);
