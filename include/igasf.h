@@ -118,9 +118,7 @@ enum {
   IGASF_KERNEL_DEFAULT = 0,
   IGASF_KERNEL_REGISTERS = 1, /* each thread loads its factors into registers, slabs ahead */
   IGASF_KERNEL_RING = 2,      /* bulk copies into a shared-memory ring by a producer warp */
-  IGASF_KERNEL_ON_THE_FLY = 3,/* reported by igasf_describe for IGASF_GEOMETRY_ON_THE_FLY */
-  IGASF_KERNEL_SPLIT = 4      /* register prefetch, each pencil pair's stiffness streams
-                                 spread over three lanes (less state per thread) */
+  IGASF_KERNEL_ON_THE_FLY = 3 /* reported by igasf_describe for IGASF_GEOMETRY_ON_THE_FLY */
 };
 
 typedef struct igasf_plan *igasf_handle;

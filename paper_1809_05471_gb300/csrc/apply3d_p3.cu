@@ -5,13 +5,12 @@
 //   TMA ring, tile 8, 8, 4
 //   register prefetch, tile 8, 4, 4
 //   register prefetch, tile 4, 4, 4
-// IGASF_TILE_SEARCH compiles every listed shape in every variant.
+// IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Factors evaluated on the fly (FP32): tile 8, 4, 2 first, then 4, 4, 4.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
 #include "apply3d_f32g.cuh"
 #include "apply3d_f32r.cuh"
-#include "apply3d_f32s.cuh"
 
 namespace igasf {
 

@@ -5,14 +5,12 @@
 //   register prefetch, tile 4, 4, 4, FP32 capped at 4 resident blocks' registers
 //   TMA ring, tile 8, 4, 2
 //   TMA ring, tile 4, 4, 4
-//   split lanes, tile 4, 4, 4
-// IGASF_TILE_SEARCH compiles every listed shape in every variant.
+// IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Factors evaluated on the fly (FP32): tile 4, 4, 2 first, then 4, 4, 4.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
 #include "apply3d_f32g.cuh"
 #include "apply3d_f32r.cuh"
-#include "apply3d_f32s.cuh"
 
 namespace igasf {
 
@@ -27,7 +25,6 @@ int apply3d_p4(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 8, 4, 2, true>() : make_apply3d_f32<4, 8, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 4, 4, 4, true>() : make_apply3d_f32<4, 4, 4, 4>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<4, 4, 4, 4, true>() : make_apply3d_f32s<4, 4, 4, 4>();
 #else
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 2, 4, true>() : make_apply3d_f32r<4, 4, 2, 4>();
@@ -41,12 +38,6 @@ int apply3d_p4(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 8, 4, 2, true>() : make_apply3d_f32<4, 8, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 2, 2, 4, true>() : make_apply3d_f32<4, 2, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 4, 4, 2, true>() : make_apply3d_f32<4, 4, 4, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<4, 4, 4, 4, true>() : make_apply3d_f32s<4, 4, 4, 4>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<4, 4, 2, 4, true>() : make_apply3d_f32s<4, 4, 2, 4>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<4, 8, 4, 4, true>() : make_apply3d_f32s<4, 8, 4, 4>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<4, 8, 4, 2, true>() : make_apply3d_f32s<4, 8, 4, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<4, 2, 2, 4, true>() : make_apply3d_f32s<4, 2, 2, 4>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<4, 4, 4, 2, true>() : make_apply3d_f32s<4, 4, 4, 2>();
 #endif
   return n;
 }

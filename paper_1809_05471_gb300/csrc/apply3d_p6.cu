@@ -5,15 +5,12 @@
 //   register prefetch, tile 2, 2, 2, FP32 capped at 4 resident blocks' registers
 //   register prefetch, tile 4, 4, 2
 //   TMA ring, tile 4, 2, 2
-//   split lanes, tile 2, 2, 2
-//   split lanes, tile 4, 2, 2
-// IGASF_TILE_SEARCH compiles every listed shape in every variant.
+// IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Factors evaluated on the fly (FP32): tile 2, 2, 2 first, then 4, 2, 2.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
 #include "apply3d_f32g.cuh"
 #include "apply3d_f32r.cuh"
-#include "apply3d_f32s.cuh"
 
 namespace igasf {
 
@@ -28,8 +25,6 @@ int apply3d_p6(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 2, true>() : make_apply3d_f32r<6, 2, 2, 2, false, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 4, 2, true>() : make_apply3d_f32r<6, 4, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 4, 2, 2, true>() : make_apply3d_f32<6, 4, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<6, 2, 2, 2, true>() : make_apply3d_f32s<6, 2, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<6, 4, 2, 2, true>() : make_apply3d_f32s<6, 4, 2, 2>();
 #else
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 2, true>() : make_apply3d_f32r<6, 2, 2, 2, false, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 4, 2, true>() : make_apply3d_f32r<6, 4, 4, 2>();
@@ -41,11 +36,6 @@ int apply3d_p6(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 4, 2, 2, true>() : make_apply3d_f32<6, 4, 2, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 2, 2, 2, true>() : make_apply3d_f32<6, 2, 2, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 4, 4, 1, true>() : make_apply3d_f32<6, 4, 4, 1>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<6, 4, 4, 2, true>() : make_apply3d_f32s<6, 4, 4, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<6, 2, 2, 4, true>() : make_apply3d_f32s<6, 2, 2, 4>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<6, 4, 2, 2, true>() : make_apply3d_f32s<6, 4, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<6, 2, 2, 2, true>() : make_apply3d_f32s<6, 2, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<6, 4, 4, 1, true>() : make_apply3d_f32s<6, 4, 4, 1>();
 #endif
   return n;
 }

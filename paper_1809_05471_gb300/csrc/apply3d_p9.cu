@@ -5,15 +5,12 @@
 //   register prefetch, tile 2, 2, 2
 //   TMA ring, tile 2, 2, 2
 //   register prefetch, tile 2, 1, 2
-//   split lanes, tile 2, 2, 2
-//   split lanes, tile 2, 2, 1
-// IGASF_TILE_SEARCH compiles every listed shape in every variant.
+// IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Factors evaluated on the fly (FP32): tile 2, 2, 2 first, then 2, 2, 1.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
 #include "apply3d_f32g.cuh"
 #include "apply3d_f32r.cuh"
-#include "apply3d_f32s.cuh"
 
 namespace igasf {
 
@@ -28,8 +25,6 @@ int apply3d_p9(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 2, true>() : make_apply3d_f32r<9, 2, 2, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<9, 2, 2, 2, true>() : make_apply3d_f32<9, 2, 2, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 1, 2, true>() : make_apply3d_f32r<9, 2, 1, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<9, 2, 2, 2, true>() : make_apply3d_f32s<9, 2, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<9, 2, 2, 1, true>() : make_apply3d_f32s<9, 2, 2, 1>();
 #else
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 2, true>() : make_apply3d_f32r<9, 2, 2, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 1, 2, true>() : make_apply3d_f32r<9, 2, 1, 2>();
@@ -39,10 +34,6 @@ int apply3d_p9(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<9, 2, 1, 2, true>() : make_apply3d_f32<9, 2, 1, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<9, 2, 2, 1, true>() : make_apply3d_f32<9, 2, 2, 1>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<9, 2, 1, 1, true>() : make_apply3d_f32<9, 2, 1, 1>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<9, 2, 2, 2, true>() : make_apply3d_f32s<9, 2, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<9, 2, 1, 2, true>() : make_apply3d_f32s<9, 2, 1, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<9, 2, 2, 1, true>() : make_apply3d_f32s<9, 2, 2, 1>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32s<9, 2, 1, 1, true>() : make_apply3d_f32s<9, 2, 1, 1>();
 #endif
   return n;
 }

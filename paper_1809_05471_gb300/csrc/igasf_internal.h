@@ -79,7 +79,7 @@ struct ApplyKernel {
   cudaError_t (*prepare)();   // raise the dynamic shared memory limit once
 };
 
-constexpr int kMaxCandidates = 24;  // compiled shapes per (d, p, precision)
+constexpr int kMaxCandidates = 16;  // compiled shapes per (d, p, precision)
 
 // The compiled kernels for (d, p, prec), default first; returns how many.
 int list_apply_kernels(int d, int p, int prec, ApplyKernel *out, int max_out);

@@ -28,7 +28,6 @@ KERNEL_DEFAULT = 0
 KERNEL_REGISTERS = 1
 KERNEL_RING = 2
 KERNEL_ON_THE_FLY = 3
-KERNEL_SPLIT = 4
 GEOMETRY_STORED = 0
 GEOMETRY_ON_THE_FLY = 1     # FP32 applies evaluate the factors inside the tile kernel
 

@@ -157,7 +157,7 @@ def test_rejects_bad_geometry_options(lib):
     p2, _ = I.make_patch(2, 3, 4, seed=0)
     rc, _ = _setup(lib, 2, [3] * 2, p2.knots, p2.ctrl, opt=opt)
     assert rc == -4
-    for kv in (G.KERNEL_ON_THE_FLY, 5, -1):     # not selectable as kernel variants
+    for kv in (G.KERNEL_ON_THE_FLY, 4, -1):     # not selectable as kernel variants
         opt = G.Options()
         opt.kernel_variant = kv
         rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, opt=opt)
