@@ -442,18 +442,16 @@ cudaError_t launch_gather(int d, int float_vectors, const void *vpart, void *v, 
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-#define IGASF_GATHER(TT, TWO_)                                                                     \
-  return cudaLaunchKernelEx(&cfg, gather_kernel<TT, TWO_>, (const TT *)vpart, (TT *)v, N[0], N1, Ntot, \
-                            T[0], T1, T2, S[0], S1, S2, E0, E1, E2, vol)
-  if (float_vectors) {
-    if (two) IGASF_GATHER(float, true);
-    else IGASF_GATHER(float, false);
-  } else {
-    if (two) IGASF_GATHER(double, true);
-    else IGASF_GATHER(double, false);
-  }
+#define IGASF_GATHER(TT, TWO_)                                                                \
+  cudaLaunchKernelEx(&cfg, gather_kernel<TT, TWO_>, (const TT *)vpart, (TT *)v, N[0], N1, Ntot, \
+                     T[0], T1, T2, S[0], S1, S2, E0, E1, E2, vol)
+  cudaError_t e;
+  if (float_vectors)
+    e = two ? IGASF_GATHER(float, true) : IGASF_GATHER(float, false);
+  else
+    e = two ? IGASF_GATHER(double, true) : IGASF_GATHER(double, false);
 #undef IGASF_GATHER
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace igasf
