@@ -34,6 +34,20 @@
 
 namespace igasf {
 
+// Phase C: read the direction-3 tables again for the transposed sweep (1)
+// instead of keeping them in registers (0).
+#ifndef IGASF_PHASE_C_RELOAD
+#define IGASF_PHASE_C_RELOAD 0
+#endif
+
+__device__ __forceinline__ float4 lds_volatile4(const float4 *p) {
+  float4 r;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))));
+  return r;
+}
+
 // Streaming (evict-first) loads of one factor chunk.
 __device__ __forceinline__ float4 ldg_stream(const float4 *p) {
   float4 r;
@@ -266,11 +280,33 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
             const float2 g1 = ffma2(D13, d3, ffma2(D12, d2, fmul2(D11, d1)));
             const float2 g2 = ffma2(D23, d3, ffma2(D22, d2, fmul2(D12, d1)));
             const float2 g3 = ffma2(D33, d3, ffma2(D23, d2, fmul2(D13, d1)));
+            if (IGASF_PHASE_C_RELOAD) {
+              // read the tables again (volatile shared loads) instead of
+              // keeping them live across the product: fewer registers
+              const float4 *b4 = reinterpret_cast<const float4 *>(t3b + q3 * 2 * PP);
+              const float4 *d4 = reinterpret_cast<const float4 *>(t3d + q3 * 2 * PP);
 #pragma unroll
-            for (int j = 0; j < P; ++j) {
-              z0[e3 + j] = ffma2(db[j], g3, z0[e3 + j]);   // W3
-              z1[e3 + j] = ffma2(b[j], g2, z1[e3 + j]);    // W2
-              z2[e3 + j] = ffma2(b[j], g1, z2[e3 + j]);    // W1
+              for (int jj = 0; jj < PP / 2; ++jj) {
+                const float4 bb = lds_volatile4(b4 + jj), dd = lds_volatile4(d4 + jj);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const int j = 2 * jj + h;
+                  if (j < P) {
+                    const float2 bj = h ? make_float2(bb.z, bb.w) : make_float2(bb.x, bb.y);
+                    const float2 dj = h ? make_float2(dd.z, dd.w) : make_float2(dd.x, dd.y);
+                    z0[e3 + j] = ffma2(dj, g3, z0[e3 + j]);
+                    z1[e3 + j] = ffma2(bj, g2, z1[e3 + j]);
+                    z2[e3 + j] = ffma2(bj, g1, z2[e3 + j]);
+                  }
+                }
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < P; ++j) {
+                z0[e3 + j] = ffma2(db[j], g3, z0[e3 + j]);   // W3
+                z1[e3 + j] = ffma2(b[j], g2, z1[e3 + j]);    // W2
+                z2[e3 + j] = ffma2(b[j], g1, z2[e3 + j]);    // W1
+              }
             }
           } else {
             float2 uq = make_float2(0.f, 0.f);
