@@ -178,9 +178,11 @@ int igasf_apply_prec(igasf_handle h, int op, int prec, const void *u, void *v, v
 
 /*
  * As igasf_apply_prec with HOST arrays u and v (pinned memory gives the
- * fastest copies): copies u to the plan's device staging buffer, applies, copies
- * the result back and waits for `stream`. The staging buffers are allocated at
- * setup. Synchronous.
+ * fastest copies): copies u to the plan's device staging buffer, applies, and
+ * returns the result in v, then waits for `stream`. A page-locked v (from
+ * cudaHostAlloc or cudaHostRegister) is written directly by the last kernel
+ * through its device mapping; any other v receives a copy from a device
+ * staging buffer. The staging buffers are allocated at setup. Synchronous.
  */
 int igasf_apply_host(igasf_handle h, int op, int prec, const void *u_host, void *v_host,
                      void *stream);

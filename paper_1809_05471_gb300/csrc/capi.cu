@@ -481,10 +481,20 @@ int igasf_apply_host(igasf_handle h, int op, int prec, const void *u_host, void 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(var.u_stage, u_host, bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "copy u to the device");
-  int rc = igasf_apply_prec(h, op, prec, var.u_stage, var.v_stage, stream);
+  // A page-locked v (cudaHostAlloc / cudaHostRegister) is written by the
+  // gather directly through its device mapping: no staging copy back.
+  cudaPointerAttributes at;
+  void *v_dev = nullptr;
+  if (cudaPointerGetAttributes(&at, v_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer != nullptr && ((uintptr_t)at.devicePointer % prec_size(prec)) == 0)
+    v_dev = at.devicePointer;
+  cudaGetLastError();   // a pageable pointer may leave an error from the attribute query
+  int rc = igasf_apply_prec(h, op, prec, var.u_stage, v_dev ? v_dev : var.v_stage, stream);
   if (rc != IGASF_OK) return rc;
-  e = cudaMemcpyAsync(v_host, var.v_stage, bytes, cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return cuda_fail(e, "copy v to the host");
+  if (!v_dev) {
+    e = cudaMemcpyAsync(v_host, var.v_stage, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy v to the host");
+  }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
   return IGASF_OK;

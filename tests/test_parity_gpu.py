@@ -226,8 +226,12 @@ def test_apply_is_deterministic_and_host_path_matches():
             assert torch.equal(v1, v2)
             uh = torch.as_tensor(u.astype(npdt)).pin_memory()
             vh = torch.empty_like(uh).pin_memory()
-            plan.apply_host(G.STIFFNESS, uh, vh, prec=prec)
+            plan.apply_host(G.STIFFNESS, uh, vh, prec=prec)      # pinned v: written directly
             assert torch.equal(vh, v1.cpu())
+            un = u.astype(npdt)
+            vn = np.full_like(un, np.nan)                        # pageable v: staged copy
+            plan.apply_host(G.STIFFNESS, un, vn, prec=prec)
+            assert np.array_equal(vn, v1.cpu().numpy())
 
 
 def test_default_precision_apply():
