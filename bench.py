@@ -66,6 +66,25 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks (the slowest rank's time); x itself for one
+    rank. device: where the all-reduce tensor lives ("cuda" for NCCL, "cpu" for
+    gloo)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(dofs_per_rank, world, seconds_per_step):
+    """GDoF/s of the whole job: every rank applies its own replica, so the work
+    is world x the per-rank dofs in the slowest rank's time."""
+    return world * dofs_per_rank / seconds_per_step / 1e9
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -298,10 +317,7 @@ def run_igasf(args):
         ms_events = e0.elapsed_time(e1)
         k_ms, g_ms, n_timed = plan.profile_end()
         ck = clocks.stop() if clocks is not None else None
-        if world > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world, "cuda")
         return ms, k_ms / max(n_timed, 1), g_ms / max(n_timed, 1), vd, ck, ms_events
 
     peaks, peak_src = measured_peaks()
@@ -322,7 +338,7 @@ def run_igasf(args):
     # headline
     ms, k_ms, g_ms, vd, clocks, ms_ev = timed(args.op, args.prec, args.steps, args.warmup, True)
     per_step = ms / args.steps
-    value = world * N / (per_step * 1e-3) / 1e9
+    value = whole_job_rate(N, world, per_step * 1e-3)
     v_main = vd.double().cpu().numpy()
 
     # end to end through the host-buffer call (pinned host memory)
@@ -336,10 +352,7 @@ def run_igasf(args):
     for _ in range(e2e_steps):
         plan.apply_host(oc[args.op], uh, vh, prec=pc[args.prec], stream=stream)
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, "cuda")
     bio = VECTOR_BYTES[args.prec]
     e2e = {"value": round(world * N * e2e_steps / e2e_s / 1e9, 4), "unit": UNIT,
            "h2d_bytes_per_step": N * bio, "d2h_bytes_per_step": N * bio,

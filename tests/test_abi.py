@@ -193,3 +193,14 @@ def test_binding_raises_without_library(tmp_path):
             mod.load_library(str(tmp_path / "missing.so"))
     finally:
         importlib.reload(G)
+
+
+def test_rejects_patch_beyond_int32_dofs_before_reading_ctrl(lib):
+    """1302^3 dofs exceed the 32-bit dof index: refused on the host, before the
+    control points are read or any device memory is touched."""
+    p = 3
+    t = I.open_uniform_knots(p, 1300)
+    ctrl = np.zeros(3)                      # far too short: must not be read
+    rc, _ = _setup(lib, 3, [p] * 3, [t, t, t], ctrl)
+    assert rc == -4
+    assert b"too large" in lib.igasf_last_error_message()
