@@ -36,11 +36,6 @@
 
 namespace igasf {
 
-// Independent partial sums per derivative chain in phase C (1 or 2).
-#ifndef IGASF_PHASE_C_ILP
-#define IGASF_PHASE_C_ILP 1
-#endif
-
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
@@ -459,24 +454,12 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
               }
             }
             if (STIFF) {
-              // IGASF_PHASE_C_ILP = 2 splits each chain into even and odd terms
-              float2 d1 = make_float2(0.f, 0.f), d2 = d1, d3 = d1, e1 = d1, e2 = d1, e3s = d1;
+              float2 d1 = make_float2(0.f, 0.f), d2 = d1, d3 = d1;
   #pragma unroll
               for (int j = 0; j < P; ++j) {
-                if (IGASF_PHASE_C_ILP > 1 && (j & 1)) {
-                  e3s = ffma2(db[j], y0[e3 + j], e3s);
-                  e2 = ffma2(b[j], y1[e3 + j], e2);
-                  e1 = ffma2(b[j], y2[e3 + j], e1);
-                } else {
-                  d3 = ffma2(db[j], y0[e3 + j], d3);
-                  d2 = ffma2(b[j], y1[e3 + j], d2);
-                  d1 = ffma2(b[j], y2[e3 + j], d1);
-                }
-              }
-              if (IGASF_PHASE_C_ILP > 1) {
-                d3 = __fadd2_rn(d3, e3s);
-                d2 = __fadd2_rn(d2, e2);
-                d1 = __fadd2_rn(d1, e1);
+                d3 = ffma2(db[j], y0[e3 + j], d3);
+                d2 = ffma2(b[j], y1[e3 + j], d2);
+                d1 = ffma2(b[j], y2[e3 + j], d1);
               }
               const float2 D11 = make_float2(dc[0].x, dc[0].y), D12 = make_float2(dc[0].z, dc[0].w);
               const float2 D13 = make_float2(dc[1].x, dc[1].y), D22 = make_float2(dc[1].z, dc[1].w);

@@ -34,12 +34,6 @@
 
 namespace igasf {
 
-// Phase C: read the direction-3 tables again for the transposed sweep (1)
-// instead of keeping them in registers (0).
-#ifndef IGASF_PHASE_C_RELOAD
-#define IGASF_PHASE_C_RELOAD 0
-#endif
-
 __device__ __forceinline__ float4 lds_volatile4(const float4 *p) {
   float4 r;
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -100,7 +94,7 @@ struct TileF2R {
   }
 };
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL>
 __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const int tile) {
   using G = TileF2R<P, S1, S2, S3>;
   constexpr int E1 = G::E1, E2 = G::E2, E3 = G::E3;
@@ -255,24 +249,12 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
             }
           }
           if (STIFF) {
-            // IGASF_PHASE_C_ILP = 2 splits each chain into even and odd terms
-            float2 d1 = make_float2(0.f, 0.f), d2 = d1, d3 = d1, e1 = d1, e2 = d1, e3s = d1;
+            float2 d1 = make_float2(0.f, 0.f), d2 = d1, d3 = d1;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
-              if (IGASF_PHASE_C_ILP > 1 && (j & 1)) {
-                e3s = ffma2(db[j], y0[e3 + j], e3s);
-                e2 = ffma2(b[j], y1[e3 + j], e2);
-                e1 = ffma2(b[j], y2[e3 + j], e1);
-              } else {
-                d3 = ffma2(db[j], y0[e3 + j], d3);
-                d2 = ffma2(b[j], y1[e3 + j], d2);
-                d1 = ffma2(b[j], y2[e3 + j], d1);
-              }
-            }
-            if (IGASF_PHASE_C_ILP > 1) {
-              d3 = __fadd2_rn(d3, e3s);
-              d2 = __fadd2_rn(d2, e2);
-              d1 = __fadd2_rn(d1, e1);
+              d3 = ffma2(db[j], y0[e3 + j], d3);
+              d2 = ffma2(b[j], y1[e3 + j], d2);
+              d1 = ffma2(b[j], y2[e3 + j], d1);
             }
             const float2 D11 = make_float2(dc[0].x, dc[0].y), D12 = make_float2(dc[0].z, dc[0].w);
             const float2 D13 = make_float2(dc[1].x, dc[1].y), D22 = make_float2(dc[1].z, dc[1].w);
@@ -280,7 +262,7 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
             const float2 g1 = ffma2(D13, d3, ffma2(D12, d2, fmul2(D11, d1)));
             const float2 g2 = ffma2(D23, d3, ffma2(D22, d2, fmul2(D12, d1)));
             const float2 g3 = ffma2(D33, d3, ffma2(D23, d2, fmul2(D13, d1)));
-            if (IGASF_PHASE_C_RELOAD) {
+            if constexpr (RL) {
               // read the tables again (volatile shared loads) instead of
               // keeping them live across the product: fewer registers
               const float4 *b4 = reinterpret_cast<const float4 *>(t3b + q3 * 2 * PP);
@@ -414,59 +396,59 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
 // Two kernel entry points per configuration: without a minimum of resident
 // blocks (the register allocator's own choice) and with one (MINB > 0 caps the
 // registers per thread at 65536 / (MINB * threads)); the launch picks by MINB.
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
 apply3d_f32r_kernel(const ApplyParams prm) {
   pdl_allow_dependents();
-  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(prm, blockIdx.x);
+  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF, RL>(prm, blockIdx.x);
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int MINB>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL, int MINB>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT, MINB)
 apply3d_f32r_kernel_mb(const ApplyParams prm) {
   pdl_allow_dependents();
-  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(prm, blockIdx.x);
+  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF, RL>(prm, blockIdx.x);
 }
 
 // Many patches in one launch: block b works on tile b - first_block[patch] of
 // patch = block_patch[b], with that patch's parameters.
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
 apply3d_f32r_batched(const BatchParams bp) {
   const int patch = bp.block_patch[blockIdx.x];
-  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
+  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF, RL>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int MINB>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL, int MINB>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT, MINB)
 apply3d_f32r_batched_mb(const BatchParams bp) {
   const int patch = bp.block_patch[blockIdx.x];
-  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
+  apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF, RL>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int MINB>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL, int MINB>
 cudaError_t launch_apply3d_f32r(const ApplyParams &prm, cudaStream_t s) {
   using G = TileF2R<P, S1, S2, S3>;
   const size_t sh = G::smem_floats(STIFF) * sizeof(float);
   if constexpr (MINB > 0)
-    apply3d_f32r_kernel_mb<P, S1, S2, S3, STIFF, PD, BF, MINB><<<prm.ntiles, G::NT, sh, s>>>(prm);
+    apply3d_f32r_kernel_mb<P, S1, S2, S3, STIFF, PD, BF, RL, MINB><<<prm.ntiles, G::NT, sh, s>>>(prm);
   else
-    apply3d_f32r_kernel<P, S1, S2, S3, STIFF, PD, BF><<<prm.ntiles, G::NT, sh, s>>>(prm);
+    apply3d_f32r_kernel<P, S1, S2, S3, STIFF, PD, BF, RL><<<prm.ntiles, G::NT, sh, s>>>(prm);
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int MINB>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL, int MINB>
 cudaError_t launch_apply3d_f32r_batched(const BatchParams &bp, int blocks, cudaStream_t s) {
   using G = TileF2R<P, S1, S2, S3>;
   const size_t sh = G::smem_floats(STIFF) * sizeof(float);
   if constexpr (MINB > 0)
-    apply3d_f32r_batched_mb<P, S1, S2, S3, STIFF, PD, BF, MINB><<<blocks, G::NT, sh, s>>>(bp);
+    apply3d_f32r_batched_mb<P, S1, S2, S3, STIFF, PD, BF, RL, MINB><<<blocks, G::NT, sh, s>>>(bp);
   else
-    apply3d_f32r_batched<P, S1, S2, S3, STIFF, PD, BF><<<blocks, G::NT, sh, s>>>(bp);
+    apply3d_f32r_batched<P, S1, S2, S3, STIFF, PD, BF, RL><<<blocks, G::NT, sh, s>>>(bp);
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, int PD, bool BF, int MINB>
+template <int P, int S1, int S2, int S3, int PD, bool BF, bool RL, int MINB>
 cudaError_t prepare_apply3d_f32r() {
   using G = TileF2R<P, S1, S2, S3>;
   const int sm = (int)(G::smem_floats(false) * sizeof(float));
@@ -474,22 +456,24 @@ cudaError_t prepare_apply3d_f32r() {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
   if constexpr (MINB > 0) {
-    e = cudaFuncSetAttribute(apply3d_f32r_kernel_mb<P, S1, S2, S3, false, PD, BF, MINB>, a, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel_mb<P, S1, S2, S3, true, PD, BF, MINB>, a, sk);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched_mb<P, S1, S2, S3, false, PD, BF, MINB>, a, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched_mb<P, S1, S2, S3, true, PD, BF, MINB>, a, sk);
+    e = cudaFuncSetAttribute(apply3d_f32r_kernel_mb<P, S1, S2, S3, false, PD, BF, RL, MINB>, a, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel_mb<P, S1, S2, S3, true, PD, BF, RL, MINB>, a, sk);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched_mb<P, S1, S2, S3, false, PD, BF, RL, MINB>, a, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched_mb<P, S1, S2, S3, true, PD, BF, RL, MINB>, a, sk);
   } else {
-    e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, false, PD, BF>, a, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, true, PD, BF>, a, sk);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF>, a, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF>, a, sk);
+    e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, false, PD, BF, RL>, a, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, true, PD, BF, RL>, a, sk);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF, RL>, a, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF, RL>, a, sk);
   }
   return e;
 }
 
 // BF: bfloat16-stored factors. PD: slabs prefetched ahead. MINB: minimum
 // resident blocks per SM asked of the register allocator (0: its own choice).
-template <int P, int S1, int S2, int S3, bool BF = false, int PD = 2, int MINB = 0>
+// RL: phase C reads the direction-3 tables again for the transposed sweep
+// instead of keeping them live across the product.
+template <int P, int S1, int S2, int S3, bool BF = false, int PD = 2, int MINB = 0, bool RL = false>
 ApplyKernel make_apply3d_f32r() {
   using G = TileF2R<P, S1, S2, S3>;
   static_assert(G::NT <= 1024, "tile too large for one block");
@@ -504,11 +488,11 @@ ApplyKernel make_apply3d_f32r() {
   k.plane = G::PL;
   k.lanes = 2;
   k.variant = IGASF_KERNEL_REGISTERS;
-  k.launch[IGASF_MASS] = &launch_apply3d_f32r<P, S1, S2, S3, false, PD, BF, MINB>;
-  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32r<P, S1, S2, S3, true, PD, BF, MINB>;
-  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF, MINB>;
-  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF, MINB>;
-  k.prepare = &prepare_apply3d_f32r<P, S1, S2, S3, PD, BF, MINB>;
+  k.launch[IGASF_MASS] = &launch_apply3d_f32r<P, S1, S2, S3, false, PD, BF, RL, MINB>;
+  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32r<P, S1, S2, S3, true, PD, BF, RL, MINB>;
+  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF, RL, MINB>;
+  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF, RL, MINB>;
+  k.prepare = &prepare_apply3d_f32r<P, S1, S2, S3, PD, BF, RL, MINB>;
   return k;
 }
 
