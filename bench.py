@@ -131,8 +131,8 @@ def sources_digest(names):
 
 def traffic_record(kernel_key):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current sources of that kernel (the kernel template, what it includes, and
-    the file that instantiates the default candidate); else None."""
+    current sources of that kernel (the kernel template and what it includes)
+    and the default candidate is still the profiled instantiation; else None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
@@ -144,9 +144,11 @@ def traffic_record(kernel_key):
         return None
     try:
         h = sources_digest(ent.get("sources", []))
+        inst = open(os.path.join(ROOT, "paper_1809_05471_gb300", "csrc",
+                                 ent.get("instantiated_in", ""))).read()
     except OSError:
         return None
-    if ent.get("sources_sha256_16") != h:
+    if ent.get("sources_sha256_16") != h or ent.get("instantiation", "\0") not in inst:
         return None
     return ent.get("dram_bytes_per_launch")
 

@@ -1,7 +1,7 @@
 // 3D apply kernels of order p = 4. FP64: scalar kernel, tile 4, 4, 4 elements.
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
-// BF16 (bfloat16-stored factors) uses the same candidates:
+// BF16 (bfloat16-stored factors) uses the same shapes and variants:
 //   register prefetch, tile 4, 4, 4, FP32 capped at 4 resident blocks' registers, tables reloaded for the transposed sweep
 //   TMA ring, tile 8, 4, 2
 //   TMA ring, tile 4, 4, 4
@@ -22,11 +22,11 @@ int apply3d_p4(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true, 2, 0, true>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, true>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 8, 4, 2, true>() : make_apply3d_f32<4, 8, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 4, 4, 4, true>() : make_apply3d_f32<4, 4, 4, 4>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true, 2, 0, true>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, true>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 2, 4, true>() : make_apply3d_f32r<4, 4, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 8, 4, 4, true>() : make_apply3d_f32r<4, 8, 4, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 8, 4, 2, true>() : make_apply3d_f32r<4, 8, 4, 2>();

@@ -252,41 +252,17 @@ int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, 
     if (e == cudaSuccess) e = upload(&b->d_gp, b->h_gp);
   }
   // capture the launches into a graph
-  // The groups' tile kernels are independent: each is captured on its own
-  // branch stream (fork from the capture stream, join before the gather), so
-  // the graph runs them concurrently.
-  const size_t ng = b->groups.size();
-  std::vector<cudaStream_t> branch(ng, nullptr);
-  std::vector<cudaEvent_t> joined(ng, nullptr);
-  cudaEvent_t fork = nullptr;
-  auto release_branches = [&]() {
-    for (size_t i = 0; i < ng; ++i) {
-      if (branch[i]) cudaStreamDestroy(branch[i]);
-      if (joined[i]) cudaEventDestroy(joined[i]);
-    }
-    if (fork) cudaEventDestroy(fork);
-  };
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-  for (size_t i = 0; i < ng && e == cudaSuccess; ++i) {
-    e = cudaStreamCreateWithFlags(&branch[i], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&joined[i], cudaEventDisableTiming);
-  }
   if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t le = cudaEventRecord(fork, b->cap);
-    for (size_t i = 0; i < ng; ++i) {
-      auto &G = b->groups[i];
+    for (auto &G : b->groups) {
       BatchParams bp;
       bp.params = G.d_params;
       bp.block_patch = G.d_block_patch;
       bp.first_block = G.d_first_block;
-      if (le == cudaSuccess) le = cudaStreamWaitEvent(branch[i], fork, 0);
-      if (le == cudaSuccess) le = G.k.launch_batched[op](bp, G.blocks, branch[i]);
-      if (le == cudaSuccess) le = cudaEventRecord(joined[i], branch[i]);
-      if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap, joined[i], 0);
+      const cudaError_t le = G.k.launch_batched[op](bp, G.blocks, b->cap);
+      if (le != cudaSuccess && e == cudaSuccess) e = le;
     }
-    if (le != cudaSuccess) e = le;
     if (vectors_are_float(prec))
       batched_gather_kernel<float><<<b->gblocks, kGatherThreads, 0, b->cap>>>(b->d_gp, b->d_gblock_patch,
                                                                             b->d_gfirst);
@@ -296,7 +272,6 @@ int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, 
     const cudaError_t ce = cudaStreamEndCapture(b->cap, &b->graph);
     if (e == cudaSuccess) e = ce;
   }
-  release_branches();
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
   if (e != cudaSuccess) {
     free_batch(b);
