@@ -39,6 +39,16 @@ namespace igasf {
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
+// Shared-memory load the compiler may not merge with an earlier load of the
+// same address (keeps a value out of registers between two uses).
+__device__ __forceinline__ float4 lds_volatile4(const float4 *p) {
+  float4 r;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))));
+  return r;
+}
+
 // ---- stored factor chunks of one pencil pair (layout.h: [chunk][unit][CE]) ----
 // FP32: a float4 holds two fields of both pencils (stiffness, three chunks), a
 // float2 the one mass field of both pencils. bfloat16: the same values in half
@@ -253,7 +263,7 @@ struct TileF2 {
   }
 };
 
-template <int P, int S1, int S2, int S3, bool STIFF, bool BF>
+template <int P, int S1, int S2, int S3, bool STIFF, bool BF, bool RL>
 __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const int first_tile,
                                                  const int tile_stride, const int tile_end) {
   using G = TileF2<P, S1, S2, S3>;
@@ -467,11 +477,33 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
               const float2 g1 = ffma2(D13, d3, ffma2(D12, d2, fmul2(D11, d1)));
               const float2 g2 = ffma2(D23, d3, ffma2(D22, d2, fmul2(D12, d1)));
               const float2 g3 = ffma2(D33, d3, ffma2(D23, d2, fmul2(D13, d1)));
+              if constexpr (RL) {
+                // read the tables again rather than keep them live (see the
+                // register-prefetch kernel)
+                const float4 *b4 = reinterpret_cast<const float4 *>(t3b + q3 * 2 * PP);
+                const float4 *d4 = reinterpret_cast<const float4 *>(t3d + q3 * 2 * PP);
   #pragma unroll
-              for (int j = 0; j < P; ++j) {
-                z0[e3 + j] = ffma2(db[j], g3, z0[e3 + j]);   // W3
-                z1[e3 + j] = ffma2(b[j], g2, z1[e3 + j]);    // W2
-                z2[e3 + j] = ffma2(b[j], g1, z2[e3 + j]);    // W1
+                for (int jj = 0; jj < PP / 2; ++jj) {
+                  const float4 bb = lds_volatile4(b4 + jj), dd = lds_volatile4(d4 + jj);
+  #pragma unroll
+                  for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * jj + h;
+                    if (j < P) {
+                      const float2 bj = h ? make_float2(bb.z, bb.w) : make_float2(bb.x, bb.y);
+                      const float2 dj = h ? make_float2(dd.z, dd.w) : make_float2(dd.x, dd.y);
+                      z0[e3 + j] = ffma2(dj, g3, z0[e3 + j]);
+                      z1[e3 + j] = ffma2(bj, g2, z1[e3 + j]);
+                      z2[e3 + j] = ffma2(bj, g1, z2[e3 + j]);
+                    }
+                  }
+                }
+              } else {
+  #pragma unroll
+                for (int j = 0; j < P; ++j) {
+                  z0[e3 + j] = ffma2(db[j], g3, z0[e3 + j]);   // W3
+                  z1[e3 + j] = ffma2(b[j], g2, z1[e3 + j]);    // W2
+                  z2[e3 + j] = ffma2(b[j], g1, z2[e3 + j]);    // W1
+                }
               }
             } else {
               float2 uq = make_float2(0.f, 0.f);
@@ -582,53 +614,54 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
   }
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, bool BF>
+template <int P, int S1, int S2, int S3, bool STIFF, bool BF, bool RL>
 __global__ void __launch_bounds__(TileF2<P, S1, S2, S3>::NT)
 apply3d_f32_kernel(const ApplyParams prm) {
   pdl_allow_dependents();
-  apply3d_f32_body<P, S1, S2, S3, STIFF, BF>(prm, blockIdx.x, gridDim.x, prm.ntiles);
+  apply3d_f32_body<P, S1, S2, S3, STIFF, BF, RL>(prm, blockIdx.x, gridDim.x, prm.ntiles);
 }
 
 // Many patches in one launch: block b works on tile b - first_block[patch] of
 // patch = block_patch[b], with that patch's parameters.
-template <int P, int S1, int S2, int S3, bool STIFF, bool BF>
+template <int P, int S1, int S2, int S3, bool STIFF, bool BF, bool RL>
 __global__ void __launch_bounds__(TileF2<P, S1, S2, S3>::NT)
 apply3d_f32_batched(const BatchParams bp) {
   const int patch = bp.block_patch[blockIdx.x];
   const int tile = blockIdx.x - bp.first_block[patch];
-  apply3d_f32_body<P, S1, S2, S3, STIFF, BF>(bp.params[patch], tile, 1, tile + 1);
+  apply3d_f32_body<P, S1, S2, S3, STIFF, BF, RL>(bp.params[patch], tile, 1, tile + 1);
 }
 
 // One block per tile (a persistent grid that walks tiles with a stride was
 // measured slower on this workload; the body supports both).
-template <int P, int S1, int S2, int S3, bool STIFF, bool BF>
+template <int P, int S1, int S2, int S3, bool STIFF, bool BF, bool RL>
 cudaError_t launch_apply3d_f32(const ApplyParams &prm, cudaStream_t s) {
   using G = TileF2<P, S1, S2, S3>;
-  apply3d_f32_kernel<P, S1, S2, S3, STIFF, BF><<<prm.ntiles, G::NT, G::smem_bytes(STIFF, BF), s>>>(prm);
+  apply3d_f32_kernel<P, S1, S2, S3, STIFF, BF, RL><<<prm.ntiles, G::NT, G::smem_bytes(STIFF, BF), s>>>(prm);
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, bool BF>
+template <int P, int S1, int S2, int S3, bool STIFF, bool BF, bool RL>
 cudaError_t launch_apply3d_f32_batched(const BatchParams &bp, int blocks, cudaStream_t s) {
   using G = TileF2<P, S1, S2, S3>;
-  apply3d_f32_batched<P, S1, S2, S3, STIFF, BF><<<blocks, G::NT, G::smem_bytes(STIFF, BF), s>>>(bp);
+  apply3d_f32_batched<P, S1, S2, S3, STIFF, BF, RL><<<blocks, G::NT, G::smem_bytes(STIFF, BF), s>>>(bp);
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, bool BF>
+template <int P, int S1, int S2, int S3, bool BF, bool RL>
 cudaError_t prepare_apply3d_f32() {
   using G = TileF2<P, S1, S2, S3>;
   const int sm = (int)G::smem_bytes(false, BF), sk = (int)G::smem_bytes(true, BF);
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, false, BF>, a, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, true, BF>, a, sk);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_batched<P, S1, S2, S3, false, BF>, a, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_batched<P, S1, S2, S3, true, BF>, a, sk);
+  cudaError_t e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, false, BF, RL>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_kernel<P, S1, S2, S3, true, BF, RL>, a, sk);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_batched<P, S1, S2, S3, false, BF, RL>, a, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32_batched<P, S1, S2, S3, true, BF, RL>, a, sk);
   return e;
 }
 
-// BF = true: the same kernel reading bfloat16-stored factors.
-template <int P, int S1, int S2, int S3, bool BF = false>
+// BF = true: the same kernel reading bfloat16-stored factors. RL: phase C reads
+// the direction-3 tables again for the transposed sweep.
+template <int P, int S1, int S2, int S3, bool BF = false, bool RL = false>
 ApplyKernel make_apply3d_f32() {
   using G = TileF2<P, S1, S2, S3>;
   static_assert(G::NT <= 1024, "tile too large for one block");
@@ -644,11 +677,11 @@ ApplyKernel make_apply3d_f32() {
   k.plane = G::PL;
   k.lanes = 2;
   k.variant = IGASF_KERNEL_RING;
-  k.launch[IGASF_MASS] = &launch_apply3d_f32<P, S1, S2, S3, false, BF>;
-  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32<P, S1, S2, S3, true, BF>;
-  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32_batched<P, S1, S2, S3, false, BF>;
-  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32_batched<P, S1, S2, S3, true, BF>;
-  k.prepare = &prepare_apply3d_f32<P, S1, S2, S3, BF>;
+  k.launch[IGASF_MASS] = &launch_apply3d_f32<P, S1, S2, S3, false, BF, RL>;
+  k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32<P, S1, S2, S3, true, BF, RL>;
+  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32_batched<P, S1, S2, S3, false, BF, RL>;
+  k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32_batched<P, S1, S2, S3, true, BF, RL>;
+  k.prepare = &prepare_apply3d_f32<P, S1, S2, S3, BF, RL>;
   return k;
 }
 

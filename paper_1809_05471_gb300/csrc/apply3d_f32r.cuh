@@ -34,13 +34,6 @@
 
 namespace igasf {
 
-__device__ __forceinline__ float4 lds_volatile4(const float4 *p) {
-  float4 r;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))));
-  return r;
-}
 
 // Streaming (evict-first) loads of one factor chunk.
 __device__ __forceinline__ float4 ldg_stream(const float4 *p) {
