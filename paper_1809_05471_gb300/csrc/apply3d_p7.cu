@@ -2,7 +2,7 @@
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
 // BF16 (bfloat16-stored factors) uses the same shapes and variants:
-//   TMA ring, tile 2, 2, 4
+//   TMA ring, tile 2, 2, 4, tables reloaded for the transposed sweep
 //   register prefetch, tile 2, 2, 4
 //   register prefetch, tile 4, 2, 2
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
@@ -22,11 +22,11 @@ int apply3d_p7(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 4, true>() : make_apply3d_f32<7, 2, 2, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 4, true, true>() : make_apply3d_f32<7, 2, 2, 4, false, true>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 2, 2, 4, true>() : make_apply3d_f32r<7, 2, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 4, 2, 2, true>() : make_apply3d_f32r<7, 4, 2, 2>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 4, true>() : make_apply3d_f32<7, 2, 2, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 4, true, true>() : make_apply3d_f32<7, 2, 2, 4, false, true>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 2, 2, 4, true>() : make_apply3d_f32r<7, 2, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 4, 2, 2, true>() : make_apply3d_f32r<7, 4, 2, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 2, 2, 1, true>() : make_apply3d_f32r<7, 2, 2, 1>();
