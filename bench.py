@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--op", default="stiffness", choices=["stiffness", "mass"])
     ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--dim", type=int, default=3, choices=[2, 3],
+                    help="2: the square counterpart of the workload (no bfloat16 or on-the-fly lines)")
     ap.add_argument("--elements", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -89,10 +91,24 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def workload_name(p, K):
-    N = (K + p - 1) ** 3
+def workload_name(p, K, d=3):
+    N = (K + p - 1) ** d
+    if d == 2:
+        return ("perturbed unit square d=2, order p=%d, %d^2 elements (%d dofs, %d^2 Gauss points), "
+                "a=exp(0.5 sin 2pi x cos 2pi y), noise min(0.2/%d, Greville gap/3), seed 0"
+                % (p, K, N, p * K, K))
     return ("perturbed unit cube d=3, order p=%d, %d^3 elements (%d dofs, %d^3 Gauss points), "
             "a=exp(0.5 sin 2pi x cos 2pi y), noise 0.2/%d, seed 0" % (p, K, N, p * K, K))
+
+
+def square_patch(p, K):
+    """The 2D counterpart of the bench cube: K^2 elements, noise below a third of
+    the smallest Greville gap (a diffeomorphism at every order)."""
+    import numpy as np
+    from paper_1809_05471_gb300 import inputs as I
+    gap = float(np.diff(I.greville(I.open_uniform_knots(p, K), p)).min())
+    return I.make_patch(2, p, K, noise_amp=min(0.2 / K, gap / 3), seed=0,
+                        coef_kind=I.COEF_EXP_SIN_COS, coef_alpha=0.5)
 
 
 def measured_peaks():
@@ -269,8 +285,8 @@ def run_igasf(args):
         if world > 1:
             dist.barrier()
 
-    p, K = args.p, args.elements
-    patch, u = I.config_cube(p=p, K=K)
+    p, K, dim = args.p, args.elements, args.dim
+    patch, u = I.config_cube(p=p, K=K) if dim == 3 else square_patch(p, K)
     t0 = time.perf_counter()
     plan = G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32, G.BF16))
     torch.cuda.synchronize()
@@ -326,7 +342,7 @@ def run_igasf(args):
     hbm = float(peaks["hbm_gbs"])
 
     def roofline(op, prec, kernel_ms):
-        ab = algorithmic_bytes(op, prec, Qtot, N)
+        ab = algorithmic_bytes(op, prec, Qtot, N, dim)
         ach = ab / (kernel_ms * 1e-3) / 1e9
         r = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
              "frac": round(ach / hbm, 4), "traffic": traffic_record("%s_%s_p%d" % (op, prec, p)),
@@ -375,9 +391,10 @@ def run_igasf(args):
             extra.append({"op": op, "prec": prec, "value": round(world * N / (ms2 / steps * 1e-3) / 1e9, 4),
                           "ms_per_step": round(ms2 / steps, 5), "roofline": roofline(op, prec, k2),
                           "gather_ms": round(g2, 5)})
-        # FP32 with the factors evaluated inside the tile kernel (nothing stored)
-        geo = G.Plan.from_patch(patch, precisions=(G.FP32,), geometry=G.GEOMETRY_ON_THE_FLY)
-        for op in ("stiffness", "mass"):
+        # FP32 with the factors evaluated inside the tile kernel (nothing stored, 3D)
+        geo = G.Plan.from_patch(patch, precisions=(G.FP32,), geometry=G.GEOMETRY_ON_THE_FLY) \
+            if dim == 3 else None
+        for op in (("stiffness", "mass") if geo is not None else ()):
             ud = torch.as_tensor(u, device="cuda").float()
             vd2 = torch.empty_like(ud)
             for _ in range(10):
@@ -402,7 +419,8 @@ def run_igasf(args):
                           "gather_ms": round(g2 / max(n2, 1), 5),
                           "bytes_per_launch": 4 * 5 * N,
                           "note": "no stored factors: reads u and the control points, writes v"})
-        geo.close()
+        if geo is not None:
+            geo.close()
 
     result = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
@@ -410,11 +428,11 @@ def run_igasf(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "f32 (bf16-stored factors)"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": workload_name(p, K), "op": args.op, "precision": args.prec,
-                   "d": 3, "order": p, "elements_per_dir": K, "dofs": N, "quad_points": Qtot,
+        "config": {"workload": workload_name(p, K, dim), "op": args.op, "precision": args.prec,
+                   "d": dim, "order": p, "elements_per_dir": K, "dofs": N, "quad_points": Qtot,
                    "tile": plan.describe(pc[args.prec])["tile"],
                    "l2": "no flush: factors (%.0f MB) larger than L2 (129 MB)"
-                         % (algorithmic_bytes(args.op, args.prec, Qtot, 0) / 1e6),
+                         % (algorithmic_bytes(args.op, args.prec, Qtot, 0, dim) / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline(args.op, args.prec, k_ms),
         "gather_ms": round(g_ms, 5),
