@@ -1,26 +1,18 @@
-// 2D apply kernels for p = 2..9 (FP64, FP32, and FP32 with bfloat16-stored
-// factors); tile = 8 x 8 elements.
-#include "apply2d.cuh"
+// 2D apply kernels for p = 2..5 (candidate lists in apply2d_list.cuh); the
+// dispatch over all orders.
+#include "apply2d_list.cuh"
 
 namespace igasf {
 
-template <int P>
-static ApplyKernel get2(int prec) {
-  if (prec == IGASF_FP64) return make_apply2d<double, P, 8, 8>();
-  if (prec == IGASF_FP32) return make_apply2d<float, P, 8, 8>();
-  return make_apply2d<float, P, 8, 8, __nv_bfloat16>();
-}
+int apply2d_list_hi(int p, int prec, ApplyKernel *out, int max_out);
 
-ApplyKernel apply2d_any(int p, int prec) {
+int apply2d_list(int p, int prec, ApplyKernel *out, int max_out) {
   switch (p) {
-    case 2: return get2<2>(prec);
-    case 3: return get2<3>(prec);
-    case 4: return get2<4>(prec);
-    case 5: return get2<5>(prec);
-    case 6: return get2<6>(prec);
-    case 7: return get2<7>(prec);
-    case 8: return get2<8>(prec);
-    default: return get2<9>(prec);
+    case 2: return apply2d_candidates<2, 32, 8, 64, 8>(prec, out, max_out);
+    case 3: return apply2d_candidates<3, 64, 8, 32, 8>(prec, out, max_out);
+    case 4: return apply2d_candidates<4, 16, 8, 32, 8>(prec, out, max_out);
+    case 5: return apply2d_candidates<5, 32, 8, 64, 4>(prec, out, max_out);
+    default: return apply2d_list_hi(p, prec, out, max_out);
   }
 }
 

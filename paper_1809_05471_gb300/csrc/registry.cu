@@ -19,15 +19,12 @@ int apply3d_p6_geo(ApplyKernel *out, int max_out);
 int apply3d_p7_geo(ApplyKernel *out, int max_out);
 int apply3d_p8_geo(ApplyKernel *out, int max_out);
 int apply3d_p9_geo(ApplyKernel *out, int max_out);
-ApplyKernel apply2d_any(int p, int prec);
+int apply2d_list(int p, int prec, ApplyKernel *out, int max_out);
 
 int list_apply_kernels(int d, int p, int prec, ApplyKernel *out, int max_out) {
   if (prec < 0 || prec >= kNumPrec) return 0;
   if (p < 2 || p > IGASF_MAX_ORDER || max_out < 1) return 0;
-  if (d == 2) {
-    out[0] = apply2d_any(p, prec);
-    return 1;
-  }
+  if (d == 2) return apply2d_list(p, prec, out, max_out);
   if (d != 3) return 0;
   switch (p) {
     case 2: return apply3d_p2(prec, out, max_out);
