@@ -1,7 +1,7 @@
 // 3D apply kernels of order p = 2. FP64: scalar kernel, tile 8, 8, 8 elements.
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
-// BF16 (bfloat16-stored factors) uses the same shapes and variants:
+// BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
 //   register prefetch, tile 8, 8, 2
 //   register prefetch, tile 8, 8, 4
 //   TMA ring, tile 16, 8, 4

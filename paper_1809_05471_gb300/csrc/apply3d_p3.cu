@@ -1,9 +1,9 @@
 // 3D apply kernels of order p = 3. FP64: scalar kernel, tile 8, 4, 4 elements.
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
-// BF16 (bfloat16-stored factors) uses the same shapes and variants:
-//   TMA ring, tile 8, 8, 4
-//   register prefetch, tile 8, 4, 4
+// BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
+//   FP32: register prefetch, tile 8, 4, 4, registers capped for 4 resident blocks, tables reloaded for the transposed sweep; BF16: TMA ring, tile 8, 8, 4
+//   FP32: TMA ring, tile 8, 8, 4; BF16: register prefetch, tile 8, 4, 4
 //   register prefetch, tile 4, 4, 4
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Factors evaluated on the fly (FP32): tile 8, 4, 2 first, then 4, 4, 4.
@@ -22,12 +22,11 @@ int apply3d_p3(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32<3, 8, 8, 4>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 4, 4, true>() : make_apply3d_f32r<3, 8, 4, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 4, 4, false, 2, 4, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 4, 4, true>() : make_apply3d_f32<3, 8, 8, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 4, true>() : make_apply3d_f32r<3, 4, 4, 4>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32<3, 8, 8, 4>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 4, 4, true>() : make_apply3d_f32r<3, 8, 4, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 4, 4, false, 2, 4, true>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 4, true>() : make_apply3d_f32r<3, 4, 4, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 8, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 8, 2, true>() : make_apply3d_f32r<3, 8, 8, 2>();

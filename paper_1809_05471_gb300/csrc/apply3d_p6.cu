@@ -1,8 +1,8 @@
 // 3D apply kernels of order p = 6. FP64: scalar kernel, tile 4, 2, 2 elements.
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
-// BF16 (bfloat16-stored factors) uses the same shapes and variants:
-//   register prefetch, tile 2, 2, 2, FP32 capped at 4 resident blocks' registers
+// BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
+//   register prefetch, tile 2, 2, 2, registers capped for 4 resident blocks
 //   register prefetch, tile 4, 4, 2
 //   TMA ring, tile 4, 2, 2
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.

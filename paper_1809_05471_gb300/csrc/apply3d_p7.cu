@@ -1,7 +1,7 @@
 // 3D apply kernels of order p = 7. FP64: scalar kernel, tile 2, 2, 2 elements.
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
-// BF16 (bfloat16-stored factors) uses the same shapes and variants:
+// BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
 //   TMA ring, tile 2, 2, 4, tables reloaded for the transposed sweep
 //   register prefetch, tile 2, 2, 4
 //   register prefetch, tile 4, 2, 2
