@@ -62,6 +62,7 @@ void free_plan(igasf_plan *h) {
       cudaFree(v.tabB[a]);
       cudaFree(v.tabD[a]);
       cudaFree(v.wq32[a]);
+      cudaFree(v.gtab[a]);
     }
     cudaFree(v.ctrl32);
     cudaFree(v.vpart);
@@ -185,7 +186,7 @@ int apply_with_workspace(igasf_plan *h, int op, int prec, const void *u, void *v
   make_apply_params(h, var, op, u, ws, &prm);
   cudaError_t e = var.k.launch[op](prm, s);
   if (e != cudaSuccess) return cuda_fail(e, "apply kernel launch");
-  e = launch_gather(h->d, vectors_are_float(prec), ws, v, h->N, var.T, var.k.S, h->p, s);
+  e = launch_gather(h->d, vectors_are_float(prec), ws, v, h->N, var.T, var.k.S, h->p, var.gtab, s);
   if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
   return IGASF_OK;
 }
@@ -373,6 +374,14 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
       TRY_CUDA(launch_pad_tables(p, K[a], v.Qpad[a], h->tabD[a], v.tabD[a], vectors_are_float(prec), s),
                "pad tables");
     }
+    for (int a = 0; a < kMaxDim; ++a) {
+      std::vector<int2> gt;
+      if (a < d) gather_table(h->N[a], v.k.S[a], v.k.S[a] + p - 1, v.T[a], gt);
+      else gather_table(0, 1, 1, 1, gt);
+      TRY(alloc((void **)&v.gtab[a], sizeof(int2) * gt.size(), "gather tables"));
+      TRY_CUDA(cudaMemcpy(v.gtab[a], gt.data(), sizeof(int2) * gt.size(), cudaMemcpyHostToDevice),
+               "gather tables");
+    }
     v.vpart_bytes = (size_t)v.ntiles * vol * es;
     TRY(alloc(&v.vpart, v.vpart_bytes, "workspace"));
     TRY(alloc(&v.u_stage, (size_t)h->Ntot * es, "staging"));
@@ -459,7 +468,7 @@ int igasf_apply_prec(igasf_handle h, int op, int prec, const void *u, void *v, v
   cudaError_t e = var.k.launch[op](prm, s);
   if (e != cudaSuccess) return cuda_fail(e, "apply kernel launch");
   if (ev) cudaEventRecord(ev[1], s);
-  e = launch_gather(h->d, vectors_are_float(prec), var.vpart, v, h->N, var.T, var.k.S, h->p, s);
+  e = launch_gather(h->d, vectors_are_float(prec), var.vpart, v, h->N, var.T, var.k.S, h->p, var.gtab, s);
   if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
   if (ev) cudaEventRecord(ev[2], s);
   return IGASF_OK;

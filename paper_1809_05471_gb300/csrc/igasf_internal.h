@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "igasf.h"
 
 namespace igasf {
@@ -127,7 +129,10 @@ cudaError_t launch_pad_tables(int p, int K, int Qpad, const double *src, void *d
                               cudaStream_t s);
 cudaError_t launch_export_factors(const FactorLayout &L, int op, int64_t Qtot, const int *Q,
                                   double *out, cudaStream_t s);
+// gtab: per direction the table of gather_table (device, N_a entries; one
+// entry {0, 1 << 16} for directions beyond d)
 cudaError_t launch_gather(int d, int float_vectors, const void *vpart, void *v, const int *N,
-                          const int *T, const int *S, int p, cudaStream_t s);
+                          const int *T, const int *S, int p, int2 *const *gtab, cudaStream_t s);
+void gather_table(int N, int S, int E, int T, std::vector<int2> &out);
 
 }  // namespace igasf

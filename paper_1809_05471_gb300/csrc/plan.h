@@ -23,6 +23,7 @@ struct Variant {
   void *vpart = nullptr;
   size_t vpart_bytes = 0;
   void *u_stage = nullptr, *v_stage = nullptr;
+  int2 *gtab[kMaxDim] = {nullptr, nullptr, nullptr};   // gather tables, see gather_table
   // factors evaluated on the fly (FP32 only): no stored factors
   bool on_the_fly = false;
   float *ctrl32 = nullptr;                            // SoA [3][N]

@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "igasf_internal.h"
 #include "layout.h"
 
@@ -373,78 +376,92 @@ cudaError_t launch_export_factors(const FactorLayout &L, int op, int64_t Qtot, c
 // (the accumulation S_D^T v_D of eq. loc-basis-change), in a fixed tile order
 // so that the result is bitwise reproducible.
 // ---------------------------------------------------------------------------
-// Tiles containing index i along one direction: t*S <= i <= t*S + E - 1, 0 <= t < T.
-__device__ __forceinline__ void tile_range(int i, int S, int E, int T, int &lo, int &hi) {
-  lo = i - E + 1 > 0 ? (i - E + S) / S : 0;
-  hi = min(T - 1, i / S);
+// The tiles containing dof index i of one direction are t*S <= i <= t*S + E - 1,
+// 0 <= t < T; per direction a table gives, for every i, the first such tile
+// (.x) and (number of tiles << 16) | (i's local index in the first tile) (.y),
+// built on the host at setup (gather_table), so the kernel does no division.
+template <typename T, bool TWO>
+__global__ void gather_kernel(const T *__restrict__ vpart, T *__restrict__ v, const int2 *__restrict__ g0,
+                              const int2 *__restrict__ g1, const int2 *__restrict__ g2, int N0, int N1,
+                              int N2, int T0, int T1, int S0, int S1, int S2, int E0, int E1, int vol) {
+  pdl_wait_primary();
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i0 >= N0) return;
+  const int2 a0 = g0[i0];
+  const int c0 = a0.y >> 16, l0 = a0.y & 0xffff;
+  for (int i2 = blockIdx.z; i2 < N2; i2 += gridDim.z) {
+    const int2 a2 = g2[i2];
+    const int c2 = a2.y >> 16, l2 = a2.y & 0xffff;
+    for (int i1 = blockIdx.y; i1 < N1; i1 += gridDim.y) {
+      const int2 a1 = g1[i1];
+      const int c1 = a1.y >> 16, l1 = a1.y & 0xffff;
+      T acc = T(0);
+      if (TWO) {
+        // at most two tiles per direction: all loads first, then the sums in
+        // tile order (t2, t1, t0 ascending)
+        T x[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int k2 = c >> 2, k1 = (c >> 1) & 1, k0 = c & 1;
+          x[c] = T(0);
+          if (k2 < c2 && k1 < c1 && k0 < c0) {
+            const int64_t tile = ((int64_t)(a2.x + k2) * T1 + (a1.x + k1)) * T0 + (a0.x + k0);
+            const int loc = ((l2 - k2 * S2) * E1 + (l1 - k1 * S1)) * E0 + (l0 - k0 * S0);
+            x[c] = vpart[tile * vol + loc];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc += x[c];
+      } else {
+        for (int k2 = 0; k2 < c2; ++k2)
+          for (int k1 = 0; k1 < c1; ++k1)
+            for (int k0 = 0; k0 < c0; ++k0) {
+              const int64_t tile = ((int64_t)(a2.x + k2) * T1 + (a1.x + k1)) * T0 + (a0.x + k0);
+              const int loc = ((l2 - k2 * S2) * E1 + (l1 - k1 * S1)) * E0 + (l0 - k0 * S0);
+              acc += vpart[tile * vol + loc];
+            }
+      }
+      v[((int64_t)i2 * N1 + i1) * N0 + i0] = acc;
+    }
+  }
 }
 
-template <typename T, bool TWO>
-__global__ void gather_kernel(const T *__restrict__ vpart, T *__restrict__ v, int N0, int N1,
-                              int Ntot, int T0, int T1, int T2, int S0, int S1, int S2, int E0,
-                              int E1, int E2, int vol) {
-  pdl_wait_primary();
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= Ntot) return;
-  const int i0 = n % N0, r = n / N0;
-  const int i1 = r % N1, i2 = r / N1;
-  int lo0, hi0, lo1, hi1, lo2, hi2;
-  tile_range(i0, S0, E0, T0, lo0, hi0);
-  tile_range(i1, S1, E1, T1, lo1, hi1);
-  tile_range(i2, S2, E2, T2, lo2, hi2);
-  T acc = T(0);
-  if (TWO) {
-    // at most two tiles per direction (S >= p - 1): issue all loads at once,
-    // then add in the same tile order as the general loop below
-    T x[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int t2 = lo2 + (c >> 2), t1 = lo1 + ((c >> 1) & 1), t0 = lo0 + (c & 1);
-      x[c] = T(0);
-      if (t2 <= hi2 && t1 <= hi1 && t0 <= hi0) {
-        const int64_t tile = ((int64_t)t2 * T1 + t1) * T0 + t0;
-        const int loc = ((i2 - t2 * S2) * E1 + (i1 - t1 * S1)) * E0 + (i0 - t0 * S0);
-        x[c] = vpart[tile * vol + loc];
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc += x[c];
-  } else {
-    for (int t2 = lo2; t2 <= hi2; ++t2)
-      for (int t1 = lo1; t1 <= hi1; ++t1)
-        for (int t0 = lo0; t0 <= hi0; ++t0) {
-          const int64_t tile = ((int64_t)t2 * T1 + t1) * T0 + t0;
-          const int loc = ((i2 - t2 * S2) * E1 + (i1 - t1 * S1)) * E0 + (i0 - t0 * S0);
-          acc += vpart[tile * vol + loc];
-        }
+void gather_table(int N, int S, int E, int T, std::vector<int2> &out) {
+  out.resize(N > 0 ? N : 1);
+  if (N <= 0) {
+    out[0] = make_int2(0, 1 << 16);
+    return;
   }
-  v[n] = acc;
+  for (int i = 0; i < N; ++i) {
+    const int lo = i - E + 1 > 0 ? (i - E + S) / S : 0;
+    const int hi = std::min(T - 1, i / S);
+    out[i] = make_int2(lo, ((hi - lo + 1) << 16) | (i - lo * S));
+  }
 }
 
 cudaError_t launch_gather(int d, int float_vectors, const void *vpart, void *v, const int *N,
-                          const int *T, const int *S, int p, cudaStream_t s) {
+                          const int *T, const int *S, int p, int2 *const *gtab, cudaStream_t s) {
   const int N1 = d > 1 ? N[1] : 1, N2 = d > 2 ? N[2] : 1;
-  const int T1 = d > 1 ? T[1] : 1, T2 = d > 2 ? T[2] : 1;
+  const int T1 = d > 1 ? T[1] : 1;
   const int S1 = d > 1 ? S[1] : 1, S2 = d > 2 ? S[2] : 1;
   const int E0 = S[0] + p - 1, E1 = d > 1 ? S1 + p - 1 : 1, E2 = d > 2 ? S2 + p - 1 : 1;
   const int vol = E0 * E1 * E2;
-  const int Ntot = N[0] * N1 * N2;
   const bool two = E0 <= 2 * S[0] && E1 <= 2 * S1 && E2 <= 2 * S2;
-  const int blocks = (Ntot + 255) / 256;
   // launched with a programmatic dependency on the tile kernel before it
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(256);
+  cfg.gridDim = dim3((N[0] + 127) / 128, std::min(N1, 65535), std::min(N2, 65535));
+  cfg.blockDim = dim3(128);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-#define IGASF_GATHER(TT, TWO_)                                                                \
-  cudaLaunchKernelEx(&cfg, gather_kernel<TT, TWO_>, (const TT *)vpart, (TT *)v, N[0], N1, Ntot, \
-                     T[0], T1, T2, S[0], S1, S2, E0, E1, E2, vol)
+#define IGASF_GATHER(TT, TWO_)                                                                      \
+  cudaLaunchKernelEx(&cfg, gather_kernel<TT, TWO_>, (const TT *)vpart, (TT *)v, (const int2 *)gtab[0], \
+                     (const int2 *)gtab[1], (const int2 *)gtab[2], N[0], N1, N2, T[0], T1, S[0], S1, S2, \
+                     E0, E1, vol)
   cudaError_t e;
   if (float_vectors)
     e = two ? IGASF_GATHER(float, true) : IGASF_GATHER(float, false);
