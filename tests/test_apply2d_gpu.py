@@ -13,9 +13,9 @@ from tests.gpu_helpers import TOL, gpu_apply, oracle_full, sample_rows, scaled_e
 
 pytestmark = pytest.mark.gpu
 
-# default tile of the packed 2D kernel per order (S1, S2)
-TILE = {2: (32, 8), 3: (64, 8), 4: (16, 8), 5: (32, 8), 6: (32, 4), 7: (32, 4), 8: (16, 4), 9: (32, 4)}
-SECOND = {2: (64, 8), 3: (32, 8), 4: (32, 8), 5: (64, 4), 6: (16, 8), 7: (16, 4), 8: (8, 4), 9: (16, 4)}
+# default tile per order (S1, S2): the packed kernel, the scalar one (8 x 8) at p = 9
+TILE = {2: (32, 8), 3: (64, 8), 4: (16, 8), 5: (32, 8), 6: (32, 4), 7: (32, 4), 8: (16, 4), 9: (8, 8)}
+SECOND = {2: (64, 8), 3: (32, 8), 4: (32, 8), 5: (64, 4), 6: (16, 8), 7: (16, 4), 8: (8, 4), 9: (32, 4)}
 
 
 def _patch(p, K, seed):
