@@ -34,13 +34,9 @@ struct GatherParams {
   void *v;
   int N0, N1, Ntot;
   int T0, T1, T2, S0, S1, S2, E0, E1, E2, vol;
-  int two;   // at most two tiles per direction contain a dof
+  int two;                    // at most two tiles per direction contain a dof
+  const int2 *g[3];           // the plan's per-direction gather tables
 };
-
-__device__ __forceinline__ void tile_range_b(int i, int S, int E, int T, int &lo, int &hi) {
-  lo = i - E + 1 > 0 ? (i - E + S) / S : 0;
-  hi = min(T - 1, i / S);
-}
 
 // Same arithmetic and summation order as the single-patch gather.
 template <typename T>
@@ -53,31 +49,31 @@ __global__ void batched_gather_kernel(const GatherParams *gp, const int *block_p
   const T *vpart = static_cast<const T *>(g.vpart);
   const int i0 = n % g.N0, r = n / g.N0;
   const int i1 = r % g.N1, i2 = r / g.N1;
-  int lo0, hi0, lo1, hi1, lo2, hi2;
-  tile_range_b(i0, g.S0, g.E0, g.T0, lo0, hi0);
-  tile_range_b(i1, g.S1, g.E1, g.T1, lo1, hi1);
-  tile_range_b(i2, g.S2, g.E2, g.T2, lo2, hi2);
+  const int2 a0 = g.g[0][i0], a1 = g.g[1][i1], a2 = g.g[2][i2];
+  const int c0 = a0.y >> 16, l0 = a0.y & 0xffff;
+  const int c1 = a1.y >> 16, l1 = a1.y & 0xffff;
+  const int c2 = a2.y >> 16, l2 = a2.y & 0xffff;
   T acc = T(0);
   if (g.two) {
     T x[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      const int t2 = lo2 + (c >> 2), t1 = lo1 + ((c >> 1) & 1), t0 = lo0 + (c & 1);
+      const int k2 = c >> 2, k1 = (c >> 1) & 1, k0 = c & 1;
       x[c] = T(0);
-      if (t2 <= hi2 && t1 <= hi1 && t0 <= hi0) {
-        const int64_t tile = ((int64_t)t2 * g.T1 + t1) * g.T0 + t0;
-        const int loc = ((i2 - t2 * g.S2) * g.E1 + (i1 - t1 * g.S1)) * g.E0 + (i0 - t0 * g.S0);
+      if (k2 < c2 && k1 < c1 && k0 < c0) {
+        const int64_t tile = ((int64_t)(a2.x + k2) * g.T1 + (a1.x + k1)) * g.T0 + (a0.x + k0);
+        const int loc = ((l2 - k2 * g.S2) * g.E1 + (l1 - k1 * g.S1)) * g.E0 + (l0 - k0 * g.S0);
         x[c] = vpart[tile * g.vol + loc];
       }
     }
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc += x[c];
   } else {
-    for (int t2 = lo2; t2 <= hi2; ++t2)
-      for (int t1 = lo1; t1 <= hi1; ++t1)
-        for (int t0 = lo0; t0 <= hi0; ++t0) {
-          const int64_t tile = ((int64_t)t2 * g.T1 + t1) * g.T0 + t0;
-          const int loc = ((i2 - t2 * g.S2) * g.E1 + (i1 - t1 * g.S1)) * g.E0 + (i0 - t0 * g.S0);
+    for (int k2 = 0; k2 < c2; ++k2)
+      for (int k1 = 0; k1 < c1; ++k1)
+        for (int k0 = 0; k0 < c0; ++k0) {
+          const int64_t tile = ((int64_t)(a2.x + k2) * g.T1 + (a1.x + k1)) * g.T0 + (a0.x + k0);
+          const int loc = ((l2 - k2 * g.S2) * g.E1 + (l1 - k1 * g.S1)) * g.E0 + (l0 - k0 * g.S0);
           acc += vpart[tile * g.vol + loc];
         }
   }
@@ -223,6 +219,7 @@ int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, 
     gp.E2 = gp.S2 + h->p - 1;
     gp.vol = gp.E0 * gp.E1 * gp.E2;
     gp.two = gp.E0 <= 2 * gp.S0 && gp.E1 <= 2 * gp.S1 && gp.E2 <= 2 * gp.S2;
+    for (int a = 0; a < 3; ++a) gp.g[a] = v.gtab[a];
   }
   b->total_dofs = off;
   // device tables
