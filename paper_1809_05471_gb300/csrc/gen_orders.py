@@ -1,0 +1,107 @@
+"""Writes csrc/apply3d_p{2..9}.cu, the per-order lists of compiled 3D tile
+kernels: the FP64 kernel, the FP32/BF16 candidates (first = default, chosen by
+timing sweeps on the order-sweep workload, about 2M dofs), the shapes the
+IGASF_TILE_SEARCH build adds, and the two on-the-fly candidates.
+
+A candidate is (variant, tile[, register cap in resident blocks[, reload]]),
+variant R = register prefetch, T = TMA ring; ("pair", FP32 candidate, BF16
+candidate) gives the two precisions different defaults.
+
+    python paper_1809_05471_gb300/csrc/gen_orders.py
+"""
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+R, T = "r", "t"
+f64 = {2: "8, 8, 8", 3: "8, 4, 4", 4: "4, 4, 4", 5: "4, 2, 2", 6: "4, 2, 2", 7: "2, 2, 2", 8: "2, 2, 2", 9: "2, 1, 2"}
+main = {
+ 2: [(R, "8, 8, 2"), (R, "8, 8, 4"), (T, "16, 8, 4")],
+ 3: [("pair", (R, "8, 4, 4", 4, 1), (T, "8, 8, 4")), ("pair", (T, "8, 8, 4"), (R, "8, 4, 4")), (R, "4, 4, 4")],
+ 4: [(R, "4, 4, 4", 4, 1), (T, "8, 4, 2"), (T, "4, 4, 4")],
+ 5: [(T, "4, 4, 4"), (R, "4, 4, 4"), (R, "4, 2, 4")],
+ 6: [(R, "2, 2, 2", 4), (R, "4, 4, 2"), (T, "4, 2, 2")],
+ 7: [(T, "2, 2, 4", 0, 1), (R, "2, 2, 4"), (R, "4, 2, 2")],
+ 8: [(R, "2, 2, 2"), (T, "4, 2, 1"), (R, "2, 2, 1")],
+ 9: [(R, "2, 2, 2"), (T, "2, 2, 2"), (R, "2, 1, 2")],
+}
+search = {
+ 2: ["8, 8, 2", "8, 8, 4", "16, 8, 4", "8, 4, 8", "8, 8, 8", "16, 8, 2"],
+ 3: ["8, 4, 4", "4, 4, 4", "8, 8, 4", "8, 8, 2", "4, 4, 2", "8, 4, 2"],
+ 4: ["4, 4, 4", "4, 2, 4", "8, 4, 4", "8, 4, 2", "2, 2, 4", "4, 4, 2"],
+ 5: ["4, 4, 4", "4, 2, 4", "2, 2, 4", "4, 4, 2", "2, 2, 2", "4, 2, 2"],
+ 6: ["4, 4, 2", "2, 2, 4", "4, 2, 2", "2, 2, 2", "4, 4, 1"],
+ 7: ["2, 2, 4", "4, 2, 2", "2, 2, 1", "4, 2, 1", "2, 2, 2"],
+ 8: ["2, 2, 2", "2, 2, 1", "4, 2, 1", "2, 1, 2"],
+ 9: ["2, 2, 2", "2, 1, 2", "2, 2, 1", "2, 1, 1"],
+}
+geo = {  # factors on the fly: (tile, Z of all slabs up front)
+ 2: [("8, 8, 2", 1), ("8, 4, 4", 1)],
+ 3: [("8, 4, 2", 1), ("4, 4, 4", 1)],
+ 4: [("4, 4, 2", 1), ("4, 4, 4", 1)],
+ 5: [("4, 2, 2", 1), ("2, 2, 2", 1)],
+ 6: [("2, 2, 2", 1), ("4, 2, 2", 0)],
+ 7: [("2, 2, 2", 0), ("2, 2, 1", 0)],
+ 8: [("2, 2, 2", 0), ("2, 2, 1", 0)],
+ 9: [("2, 2, 2", 0), ("2, 2, 1", 0)],
+}
+mk = {R: "make_apply3d_f32r", T: "make_apply3d_f32"}
+name = {R: "register prefetch", T: "TMA ring"}
+for P in range(2, 10):
+    L = ["// 3D apply kernels of order p = %d. FP64: scalar kernel, tile %s elements." % (P, f64[P]),
+         "// FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep",
+         "// of tile shapes and factor-stream variants on the order-sweep workload);",
+         "// BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:"]
+    def describe(c):
+        v, t = c[0], c[1]
+        return "%s, tile %s%s%s" % (name[v], t, (", registers capped for %d resident blocks" % c[2]) if len(c) > 2 and c[2] else "",
+                                   ", tables reloaded for the transposed sweep" if len(c) > 3 and c[3] else "")
+    for c in main[P]:
+        if c[0] == "pair":
+            L.append("//   FP32: %s; BF16: %s" % (describe(c[1]), describe(c[2])))
+        else:
+            L.append("//   %s" % describe(c))
+    L.append("// IGASF_TILE_SEARCH compiles every listed shape in both variants.")
+    L.append("// Factors evaluated on the fly (FP32): tile %s first, then %s." % (geo[P][0][0], geo[P][1][0]))
+    L.append('#include "apply3d.cuh"\n#include "apply3d_f32.cuh"\n#include "apply3d_f32g.cuh"\n#include "apply3d_f32r.cuh"\n\nnamespace igasf {\n')
+    L.append("int apply3d_p%d(int prec, ApplyKernel *out, int max_out) {" % P)
+    L.append("  int n = 0;\n  if (prec == IGASF_FP64) {")
+    L.append("    if (n < max_out) out[n++] = make_apply3d<double, %d, %s>();\n    return n;\n  }" % (P, f64[P]))
+    L.append("  const bool bf = prec == IGASF_BF16;")
+    L.append("#ifndef IGASF_TILE_SEARCH")
+    def inst(c):
+        """(BF16, FP32) instantiations of a candidate (variant, tile[, minb[, reload]])."""
+        v, t = c[0], c[1]
+        minb = c[2] if len(c) > 2 else 0
+        rl = "true" if len(c) > 3 and c[3] else "false"
+        if v == R and (minb or rl == "true"):
+            # BF16 keeps the compiler's register choice and the tables in registers
+            # (both measured faster for the bfloat16 stream)
+            return ("%s<%d, %s, true>()" % (mk[v], P, t),
+                    "%s<%d, %s, false, 2, %d, %s>()" % (mk[v], P, t, minb, rl))
+        if v == T and rl == "true":
+            return ("%s<%d, %s, true, true>()" % (mk[v], P, t), "%s<%d, %s, false, true>()" % (mk[v], P, t))
+        return ("%s<%d, %s, true>()" % (mk[v], P, t), "%s<%d, %s>()" % (mk[v], P, t))
+    def inst2(c):
+        """("pair", FP32 candidate, BF16 candidate): different defaults per precision."""
+        if c[0] == "pair":
+            return inst(c[2])[0], inst(c[1])[1]
+        return inst(c)
+    for c in main[P]:
+        b16, f32 = inst2(c)
+        L.append("  if (n < max_out) out[n++] = bf ? %s : %s;" % (b16, f32))
+    L.append("#else")
+    first = main[P][0]
+    b16, f32 = inst2(first)
+    L.append("  if (n < max_out) out[n++] = bf ? %s : %s;" % (b16, f32))
+    firsts = [first[1][:2], first[2][:2]] if first[0] == "pair" else [tuple(first[:2])]
+    for v in (R, T):
+        for t in search[P]:
+            if (v, t) in [tuple(f) for f in firsts]:
+                continue
+            L.append("  if (n < max_out) out[n++] = bf ? %s<%d, %s, true>() : %s<%d, %s>();" % (mk[v], P, t, mk[v], P, t))
+    L.append("#endif\n  return n;\n}\n")
+    L.append("int apply3d_p%d_geo(ApplyKernel *out, int max_out) {\n  int n = 0;" % P)
+    for t, z in geo[P]:
+        L.append("  if (n < max_out) out[n++] = make_apply3d_f32g<%d, %s, %s>();" % (P, t, "true" if z else "false"))
+    L.append("  return n;\n}\n\n}  // namespace igasf")
+    open(os.path.join(HERE, "apply3d_p%d.cu" % P), "w").write("\n".join(L) + "\n")
