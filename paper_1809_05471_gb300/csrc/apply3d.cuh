@@ -45,6 +45,17 @@ struct Tile3 {
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
 
+// Two neighbouring values of one factor chunk in one load (a chunk holds two
+// values and starts at an even index, so the pair is aligned).
+template <typename T> struct Pair2;
+template <> struct Pair2<double> { using type = double2; };
+template <> struct Pair2<float> { using type = float2; };
+
+template <typename T>
+__device__ __forceinline__ typename Pair2<T>::type ld_stream2(const T *p) {
+  return __ldcs(reinterpret_cast<const typename Pair2<T>::type *>(p));
+}
+
 template <typename T, int P, int S1, int S2, int S3, bool STIFF>
 __device__ __forceinline__ void apply3d_body(const ApplyParams &prm, const int tile) {
   using G = Tile3<P, S1, S2, S3>;
@@ -176,12 +187,13 @@ __device__ __forceinline__ void apply3d_body(const ApplyParams &prm, const int t
           if (STIFF) {
             T D11 = T(0), D12 = T(0), D13 = T(0), D22 = T(0), D23 = T(0), D33 = T(0);
             if (valid) {
-              D11 = ld_stream(Dq);
-              D12 = ld_stream(Dq + 1);
-              D13 = ld_stream(Dq + 2 * PL);
-              D22 = ld_stream(Dq + 2 * PL + 1);
-              D23 = ld_stream(Dq + 4 * PL);
-              D33 = ld_stream(Dq + 4 * PL + 1);
+              const auto c0 = ld_stream2(Dq), c1 = ld_stream2(Dq + 2 * PL), c2 = ld_stream2(Dq + 4 * PL);
+              D11 = c0.x;
+              D12 = c0.y;
+              D13 = c1.x;
+              D22 = c1.y;
+              D23 = c2.x;
+              D33 = c2.y;
             }
             T d1 = T(0), d2 = T(0), d3 = T(0);
 #pragma unroll
