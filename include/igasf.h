@@ -345,6 +345,19 @@ int igasf_autotune(int d, const int *orders, const int *knot_lengths, const doub
                    int *tile, int *kernel_variant, double *best_ms);
 
 /*
+ * The compiled tile-kernel candidates of (d, p, prec) for the given geometry
+ * mode (IGASF_GEOMETRY_STORED or IGASF_GEOMETRY_ON_THE_FLY, the latter FP32
+ * and d = 3 only), in the order igasf_setup tries them (the first is the
+ * default). Writes, for candidate i < max_out, its tile shape to
+ * tiles[3 i .. 3 i + 2] (1 in unused directions) and its IGASF_KERNEL_* to
+ * variants[i]; either array may be NULL to only count. Each candidate is
+ * selected by passing that tile and variant in igasf_options. Host-only: no
+ * device is touched. Returns the number of candidates (0 when none is built
+ * for the combination), or a negative status for an invalid argument.
+ */
+int igasf_list_kernels(int d, int p, int prec, int geometry, int *tiles, int *variants, int max_out);
+
+/*
  * Number of stored entries of the assembled matrix: the pairs (m, n) with
  * |m_a - n_a| <= p - 1 in every direction, which for simple interior knots is
  * prod_a ((2p - 1) K_a + (p - 1)^2) (Sec. 3.2, Corollary on nnz of B-spline

@@ -2,6 +2,7 @@
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
 // BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
+//   register prefetch, tile 2, 2, 8, registers capped for 4 resident blocks, tables reloaded for the transposed sweep
 //   register prefetch, tile 2, 2, 2, registers capped for 4 resident blocks
 //   register prefetch, tile 4, 4, 2
 //   TMA ring, tile 4, 2, 2
@@ -22,20 +23,25 @@ int apply3d_p6(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 8, true>() : make_apply3d_f32r<6, 2, 2, 8, false, 2, 4, true>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 2, true>() : make_apply3d_f32r<6, 2, 2, 2, false, 2, 4, false>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 4, 2, true>() : make_apply3d_f32r<6, 4, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 4, 2, 2, true>() : make_apply3d_f32<6, 4, 2, 2>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 2, true>() : make_apply3d_f32r<6, 2, 2, 2, false, 2, 4, false>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 8, true>() : make_apply3d_f32r<6, 2, 2, 8, false, 2, 4, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 6, true>() : make_apply3d_f32r<6, 2, 2, 6>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 2, 4, true>() : make_apply3d_f32r<6, 4, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 4, 2, true>() : make_apply3d_f32r<6, 4, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 4, true>() : make_apply3d_f32r<6, 2, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 2, 2, true>() : make_apply3d_f32r<6, 4, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 4, 1, true>() : make_apply3d_f32r<6, 4, 4, 1>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 2, true>() : make_apply3d_f32r<6, 2, 2, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 2, 2, 8, true>() : make_apply3d_f32<6, 2, 2, 8>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 2, 2, 6, true>() : make_apply3d_f32<6, 2, 2, 6>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 4, 2, 4, true>() : make_apply3d_f32<6, 4, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 4, 4, 2, true>() : make_apply3d_f32<6, 4, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 2, 2, 4, true>() : make_apply3d_f32<6, 2, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 4, 2, 2, true>() : make_apply3d_f32<6, 4, 2, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 2, 2, 2, true>() : make_apply3d_f32<6, 2, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 4, 4, 1, true>() : make_apply3d_f32<6, 4, 4, 1>();
 #endif
   return n;
 }

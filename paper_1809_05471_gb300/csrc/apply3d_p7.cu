@@ -2,8 +2,9 @@
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
 // BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
+//   FP32: register prefetch, tile 2, 2, 6, registers capped for 2 resident blocks, tables reloaded for the transposed sweep; BF16: register prefetch, tile 2, 2, 8
+//   FP32: register prefetch, tile 2, 2, 8, registers capped for 3 resident blocks, tables reloaded for the transposed sweep; BF16: register prefetch, tile 2, 2, 6
 //   TMA ring, tile 2, 2, 4, tables reloaded for the transposed sweep
-//   register prefetch, tile 2, 2, 4
 //   register prefetch, tile 4, 2, 2
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Factors evaluated on the fly (FP32): tile 2, 2, 2 first, then 2, 2, 1.
@@ -22,19 +23,21 @@ int apply3d_p7(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 2, 2, 8, true>() : make_apply3d_f32r<7, 2, 2, 6, false, 2, 2, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 2, 2, 6, true>() : make_apply3d_f32r<7, 2, 2, 8, false, 2, 3, true>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 4, true, true>() : make_apply3d_f32<7, 2, 2, 4, false, true>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 2, 2, 4, true>() : make_apply3d_f32r<7, 2, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 4, 2, 2, true>() : make_apply3d_f32r<7, 4, 2, 2>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 4, true, true>() : make_apply3d_f32<7, 2, 2, 4, false, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 2, 2, 8, true>() : make_apply3d_f32r<7, 2, 2, 6, false, 2, 2, true>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 2, 2, 4, true>() : make_apply3d_f32r<7, 2, 2, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 4, 2, 4, true>() : make_apply3d_f32r<7, 4, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 4, 2, 2, true>() : make_apply3d_f32r<7, 4, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 2, 2, 1, true>() : make_apply3d_f32r<7, 2, 2, 1>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 4, 2, 1, true>() : make_apply3d_f32r<7, 4, 2, 1>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<7, 2, 2, 2, true>() : make_apply3d_f32r<7, 2, 2, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 8, true>() : make_apply3d_f32<7, 2, 2, 8>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 6, true>() : make_apply3d_f32<7, 2, 2, 6>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 4, true>() : make_apply3d_f32<7, 2, 2, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 4, 2, 4, true>() : make_apply3d_f32<7, 4, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 4, 2, 2, true>() : make_apply3d_f32<7, 4, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 1, true>() : make_apply3d_f32<7, 2, 2, 1>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 4, 2, 1, true>() : make_apply3d_f32<7, 4, 2, 1>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<7, 2, 2, 2, true>() : make_apply3d_f32<7, 2, 2, 2>();
 #endif
   return n;

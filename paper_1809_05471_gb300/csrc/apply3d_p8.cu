@@ -2,9 +2,10 @@
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
 // BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
+//   register prefetch, tile 2, 2, 8
+//   register prefetch, tile 2, 2, 6
 //   register prefetch, tile 2, 2, 2
 //   TMA ring, tile 4, 2, 1
-//   register prefetch, tile 2, 2, 1
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Factors evaluated on the fly (FP32): tile 2, 2, 2 first, then 2, 2, 1.
 #include "apply3d.cuh"
@@ -22,18 +23,21 @@ int apply3d_p8(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<8, 2, 2, 8, true>() : make_apply3d_f32r<8, 2, 2, 8>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<8, 2, 2, 6, true>() : make_apply3d_f32r<8, 2, 2, 6>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<8, 2, 2, 2, true>() : make_apply3d_f32r<8, 2, 2, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<8, 4, 2, 1, true>() : make_apply3d_f32<8, 4, 2, 1>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<8, 2, 2, 1, true>() : make_apply3d_f32r<8, 2, 2, 1>();
 #else
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<8, 2, 2, 8, true>() : make_apply3d_f32r<8, 2, 2, 8>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<8, 2, 2, 6, true>() : make_apply3d_f32r<8, 2, 2, 6>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<8, 2, 2, 4, true>() : make_apply3d_f32r<8, 2, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<8, 2, 2, 2, true>() : make_apply3d_f32r<8, 2, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<8, 2, 2, 1, true>() : make_apply3d_f32r<8, 2, 2, 1>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<8, 4, 2, 1, true>() : make_apply3d_f32r<8, 4, 2, 1>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<8, 2, 1, 2, true>() : make_apply3d_f32r<8, 2, 1, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<8, 2, 2, 8, true>() : make_apply3d_f32<8, 2, 2, 8>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<8, 2, 2, 6, true>() : make_apply3d_f32<8, 2, 2, 6>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<8, 2, 2, 4, true>() : make_apply3d_f32<8, 2, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<8, 2, 2, 2, true>() : make_apply3d_f32<8, 2, 2, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<8, 2, 2, 1, true>() : make_apply3d_f32<8, 2, 2, 1>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<8, 4, 2, 1, true>() : make_apply3d_f32<8, 4, 2, 1>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<8, 2, 1, 2, true>() : make_apply3d_f32<8, 2, 1, 2>();
 #endif
   return n;
 }

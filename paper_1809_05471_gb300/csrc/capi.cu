@@ -199,6 +199,28 @@ int igasf_version(void) { return IGASF_VERSION; }
 
 const char *igasf_last_error_message(void) { return g_last_error.c_str(); }
 
+int igasf_list_kernels(int d, int p, int prec, int geometry, int *tiles, int *variants, int max_out) {
+  g_last_error.clear();
+  if (d != 2 && d != 3) return fail(IGASF_ERR_INVALID_ARG, "d = %d (2 or 3)", d);
+  if (p < 2 || p > IGASF_MAX_ORDER) return fail(IGASF_ERR_INVALID_ARG, "p = %d (2..%d)", p, IGASF_MAX_ORDER);
+  if (prec < 0 || prec >= kNumPrec) return fail(IGASF_ERR_INVALID_ARG, "prec = %d", prec);
+  if (geometry != IGASF_GEOMETRY_STORED && geometry != IGASF_GEOMETRY_ON_THE_FLY)
+    return fail(IGASF_ERR_INVALID_ARG, "geometry = %d", geometry);
+  if (max_out < 0) return fail(IGASF_ERR_INVALID_ARG, "max_out < 0");
+  ApplyKernel cand[kMaxCandidates];
+  int n = 0;
+  if (geometry == IGASF_GEOMETRY_STORED)
+    n = list_apply_kernels(d, p, prec, cand, kMaxCandidates);
+  else if (d == 3 && prec == IGASF_FP32)
+    n = list_geometry_kernels(p, cand, kMaxCandidates);
+  for (int i = 0; i < n && i < max_out; ++i) {
+    for (int a = 0; a < 3; ++a)
+      if (tiles) tiles[3 * i + a] = a < d ? cand[i].S[a] : 1;
+    if (variants) variants[i] = cand[i].variant;
+  }
+  return n;
+}
+
 int igasf_setup(int d, const int *orders, const int *knot_lengths, const double *const *knots,
                 const double *ctrl, const igasf_coef *coef, const igasf_options *opt,
                 igasf_handle *out) {

@@ -19,20 +19,21 @@ main = {
  3: [("pair", (R, "8, 4, 4", 4, 1), (T, "8, 8, 4")), ("pair", (T, "8, 8, 4"), (R, "8, 4, 4")), (R, "4, 4, 4")],
  4: [(R, "4, 4, 4", 4, 1), (T, "8, 4, 2"), (T, "4, 4, 4")],
  5: [(T, "4, 4, 4"), (R, "4, 4, 4"), (R, "4, 2, 4")],
- 6: [(R, "2, 2, 2", 4), (R, "4, 4, 2"), (T, "4, 2, 2")],
- 7: [(T, "2, 2, 4", 0, 1), (R, "2, 2, 4"), (R, "4, 2, 2")],
- 8: [(R, "2, 2, 2"), (T, "4, 2, 1"), (R, "2, 2, 1")],
- 9: [(R, "2, 2, 2"), (T, "2, 2, 2"), (R, "2, 1, 2")],
+ 6: [(R, "2, 2, 8", 4, 1), (R, "2, 2, 2", 4), (R, "4, 4, 2"), (T, "4, 2, 2")],
+ 7: [("pair", (R, "2, 2, 6", 2, 1), (R, "2, 2, 8")), ("pair", (R, "2, 2, 8", 3, 1), (R, "2, 2, 6")),
+     (T, "2, 2, 4", 0, 1), (R, "4, 2, 2")],
+ 8: [(R, "2, 2, 8"), (R, "2, 2, 6"), (R, "2, 2, 2"), (T, "4, 2, 1")],
+ 9: [(R, "2, 2, 6", 2, 1), (R, "2, 2, 8", 2, 1), (R, "2, 2, 2", 2, 1), (T, "2, 2, 2")],
 }
 search = {
  2: ["8, 8, 2", "8, 8, 4", "16, 8, 4", "8, 4, 8", "8, 8, 8", "16, 8, 2"],
  3: ["8, 4, 4", "4, 4, 4", "8, 8, 4", "8, 8, 2", "4, 4, 2", "8, 4, 2"],
  4: ["4, 4, 4", "4, 2, 4", "8, 4, 4", "8, 4, 2", "2, 2, 4", "4, 4, 2"],
  5: ["4, 4, 4", "4, 2, 4", "2, 2, 4", "4, 4, 2", "2, 2, 2", "4, 2, 2"],
- 6: ["4, 4, 2", "2, 2, 4", "4, 2, 2", "2, 2, 2", "4, 4, 1"],
- 7: ["2, 2, 4", "4, 2, 2", "2, 2, 1", "4, 2, 1", "2, 2, 2"],
- 8: ["2, 2, 2", "2, 2, 1", "4, 2, 1", "2, 1, 2"],
- 9: ["2, 2, 2", "2, 1, 2", "2, 2, 1", "2, 1, 1"],
+ 6: ["2, 2, 8", "2, 2, 6", "4, 2, 4", "4, 4, 2", "2, 2, 4", "4, 2, 2", "2, 2, 2"],
+ 7: ["2, 2, 8", "2, 2, 6", "2, 2, 4", "4, 2, 4", "4, 2, 2", "2, 2, 2"],
+ 8: ["2, 2, 8", "2, 2, 6", "2, 2, 4", "2, 2, 2", "4, 2, 1"],
+ 9: ["2, 2, 8", "2, 2, 6", "2, 2, 4", "2, 2, 2", "2, 1, 2"],
 }
 geo = {  # factors on the fly: (tile, Z of all slabs up front)
  2: [("8, 8, 2", 1), ("8, 4, 4", 1)],

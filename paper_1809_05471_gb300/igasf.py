@@ -16,6 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libigasf.so")
 
 OK = 0
+ERR_INVALID_ARG = -1
+MAX_ORDER = 9   # IGASF_MAX_ORDER: the orders the kernels are built for, 2..9
 MASS = 0
 STIFFNESS = 1
 FP64 = 0
@@ -43,7 +45,7 @@ EXPORTED = [
     "igasf_get_factors", "igasf_profile_begin", "igasf_profile_end", "igasf_apply_noalloc",
     "igasf_device_status", "igasf_set_test_fault", "igasf_cg_solve",
     "igasf_batch_create", "igasf_batch_apply", "igasf_batch_info", "igasf_batch_destroy",
-    "igasf_autotune", "igasf_assembled_nnz", "igasf_assemble_csr",
+    "igasf_autotune", "igasf_list_kernels", "igasf_assembled_nnz", "igasf_assemble_csr",
     "igasf_last_error_message", "igasf_version",
 ]
 
@@ -117,6 +119,8 @@ def load_library(path: str = LIB_PATH):
     lib.igasf_batch_destroy.argtypes = [vp]
     lib.igasf_autotune.argtypes = [ctypes.c_int, ip, ip, ctypes.POINTER(dp), dp, ctypes.POINTER(Coef),
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip, dp]
+    lib.igasf_list_kernels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip,
+                                       ctypes.c_int]
     lib.igasf_assembled_nnz.argtypes = [vp]
     lib.igasf_assembled_nnz.restype = ctypes.c_int64
     lib.igasf_assemble_csr.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_size_t, vp]
@@ -322,6 +326,18 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def list_kernels(d: int, p: int, prec: int, geometry: int = GEOMETRY_STORED):
+    """The compiled (tile, kernel variant) candidates of (d, p, prec), default first."""
+    lib = load_library()
+    n = lib.igasf_list_kernels(int(d), int(p), int(prec), int(geometry), None, None, 0)
+    if n < 0:
+        _check(n)
+    tiles = (ctypes.c_int * (3 * max(n, 1)))()
+    variants = (ctypes.c_int * max(n, 1))()
+    lib.igasf_list_kernels(int(d), int(p), int(prec), int(geometry), tiles, variants, n)
+    return [(list(tiles[3 * i:3 * i + 3]), int(variants[i])) for i in range(n)]
 
 
 def autotune(patch, op: int = STIFFNESS, prec: int = FP32, repeats: int = 5):

@@ -204,3 +204,33 @@ def test_rejects_patch_beyond_int32_dofs_before_reading_ctrl(lib):
     rc, _ = _setup(lib, 3, [p] * 3, [t, t, t], ctrl)
     assert rc == -4
     assert b"too large" in lib.igasf_last_error_message()
+
+
+def test_list_kernels_enumerates_selectable_candidates(lib):
+    """Host-only listing: every (d, p, precision) has a default, each (tile,
+    variant) appears once per list, unused directions read 1, the on-the-fly
+    list exists for FP32 in 3D only, and bad arguments are rejected."""
+    for d in (2, 3):
+        for p in range(2, G.MAX_ORDER + 1):
+            for prec in (G.FP64, G.FP32, G.BF16):
+                cands = G.list_kernels(d, p, prec)
+                assert len(cands) >= 1
+                keys = [(tuple(t), v) for t, v in cands]
+                assert len(set(keys)) == len(keys)
+                for t, v in cands:
+                    assert all(s >= 1 for s in t[:d]) and all(s == 1 for s in t[d:])
+                    assert v in (G.KERNEL_REGISTERS, G.KERNEL_RING)
+                if prec == G.FP64:
+                    assert all(v == G.KERNEL_REGISTERS for _, v in cands)
+            geo = G.list_kernels(d, p, G.FP32, G.GEOMETRY_ON_THE_FLY)
+            assert (len(geo) >= 1) == (d == 3)
+            assert all(v == G.KERNEL_ON_THE_FLY for _, v in geo)
+            assert G.list_kernels(d, p, G.FP64, G.GEOMETRY_ON_THE_FLY) == []
+    # the documented default of the benchmark workload's order
+    assert G.list_kernels(3, 4, G.FP32)[0] == ([4, 4, 4], G.KERNEL_REGISTERS)
+    n = lib.igasf_list_kernels(3, 4, G.FP32, 0, None, None, 0)
+    assert n == len(G.list_kernels(3, 4, G.FP32))
+    for args in [(4, 3, 0, 0), (3, 1, 0, 0), (3, G.MAX_ORDER + 1, 0, 0), (3, 4, 7, 0), (3, 4, 1, 5)]:
+        with pytest.raises(G.IgasfError):
+            G.list_kernels(*args)
+    assert lib.igasf_list_kernels(3, 4, G.FP32, 0, None, None, -1) == G.ERR_INVALID_ARG
