@@ -2,12 +2,12 @@
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
 // BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
-//   register prefetch, tile 2, 2, 8, registers capped for 4 resident blocks, tables reloaded for the transposed sweep
+//   register prefetch, tile 2, 2, 8, registers capped for 4 resident blocks, tables reloaded for the transposed sweep (BF16 too)
 //   register prefetch, tile 2, 2, 2, registers capped for 4 resident blocks
 //   register prefetch, tile 4, 4, 2
 //   TMA ring, tile 4, 2, 2
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
-// Factors evaluated on the fly (FP32): tile 2, 2, 2 first, then 4, 2, 2.
+// Factors evaluated on the fly (FP32): tile 2, 2, 8 first, then 2, 2, 2.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
 #include "apply3d_f32g.cuh"
@@ -23,12 +23,12 @@ int apply3d_p6(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 8, true>() : make_apply3d_f32r<6, 2, 2, 8, false, 2, 4, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 8, true, 2, 4, true>() : make_apply3d_f32r<6, 2, 2, 8, false, 2, 4, true>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 2, true>() : make_apply3d_f32r<6, 2, 2, 2, false, 2, 4, false>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 4, 2, true>() : make_apply3d_f32r<6, 4, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 4, 2, 2, true>() : make_apply3d_f32<6, 4, 2, 2>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 8, true>() : make_apply3d_f32r<6, 2, 2, 8, false, 2, 4, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 8, true, 2, 4, true>() : make_apply3d_f32r<6, 2, 2, 8, false, 2, 4, true>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 6, true>() : make_apply3d_f32r<6, 2, 2, 6>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 2, 4, true>() : make_apply3d_f32r<6, 4, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 4, 2, true>() : make_apply3d_f32r<6, 4, 4, 2>();
@@ -48,8 +48,8 @@ int apply3d_p6(int prec, ApplyKernel *out, int max_out) {
 
 int apply3d_p6_geo(ApplyKernel *out, int max_out) {
   int n = 0;
+  if (n < max_out) out[n++] = make_apply3d_f32g<6, 2, 2, 8, false>();
   if (n < max_out) out[n++] = make_apply3d_f32g<6, 2, 2, 2, true>();
-  if (n < max_out) out[n++] = make_apply3d_f32g<6, 4, 2, 2, false>();
   return n;
 }
 

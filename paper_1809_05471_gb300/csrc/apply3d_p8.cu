@@ -7,7 +7,7 @@
 //   register prefetch, tile 2, 2, 2
 //   TMA ring, tile 4, 2, 1
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
-// Factors evaluated on the fly (FP32): tile 2, 2, 2 first, then 2, 2, 1.
+// Factors evaluated on the fly (FP32): tile 2, 2, 4 first, then 2, 2, 2.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
 #include "apply3d_f32g.cuh"
@@ -44,8 +44,8 @@ int apply3d_p8(int prec, ApplyKernel *out, int max_out) {
 
 int apply3d_p8_geo(ApplyKernel *out, int max_out) {
   int n = 0;
+  if (n < max_out) out[n++] = make_apply3d_f32g<8, 2, 2, 4, false>();
   if (n < max_out) out[n++] = make_apply3d_f32g<8, 2, 2, 2, false>();
-  if (n < max_out) out[n++] = make_apply3d_f32g<8, 2, 2, 1, false>();
   return n;
 }
 

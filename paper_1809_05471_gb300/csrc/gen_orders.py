@@ -3,9 +3,10 @@ kernels: the FP64 kernel, the FP32/BF16 candidates (first = default, chosen by
 timing sweeps on the order-sweep workload, about 2M dofs), the shapes the
 IGASF_TILE_SEARCH build adds, and the two on-the-fly candidates.
 
-A candidate is (variant, tile[, register cap in resident blocks[, reload]]),
-variant R = register prefetch, T = TMA ring; ("pair", FP32 candidate, BF16
-candidate) gives the two precisions different defaults.
+A candidate is (variant, tile[, register cap in resident blocks[, reload[, BF16
+too]]]), variant R = register prefetch, T = TMA ring; the cap and the reload apply
+to FP32 only unless the last flag is set; ("pair", FP32 candidate, BF16 candidate)
+gives the two precisions different defaults.
 
     python paper_1809_05471_gb300/csrc/gen_orders.py
 """
@@ -19,11 +20,11 @@ main = {
  3: [("pair", (R, "8, 4, 4", 4, 1), (T, "8, 8, 4")), ("pair", (T, "8, 8, 4"), (R, "8, 4, 4")), (R, "4, 4, 4")],
  4: [(R, "4, 4, 4", 4, 1), (T, "8, 4, 2"), (T, "4, 4, 4")],
  5: [(T, "4, 4, 4"), (R, "4, 4, 4"), (R, "4, 2, 4")],
- 6: [(R, "2, 2, 8", 4, 1), (R, "2, 2, 2", 4), (R, "4, 4, 2"), (T, "4, 2, 2")],
+ 6: [(R, "2, 2, 8", 4, 1, 1), (R, "2, 2, 2", 4), (R, "4, 4, 2"), (T, "4, 2, 2")],
  7: [("pair", (R, "2, 2, 6", 2, 1), (R, "2, 2, 8")), ("pair", (R, "2, 2, 8", 3, 1), (R, "2, 2, 6")),
      (T, "2, 2, 4", 0, 1), (R, "4, 2, 2")],
  8: [(R, "2, 2, 8"), (R, "2, 2, 6"), (R, "2, 2, 2"), (T, "4, 2, 1")],
- 9: [(R, "2, 2, 6", 2, 1), (R, "2, 2, 8", 2, 1), (R, "2, 2, 2", 2, 1), (T, "2, 2, 2")],
+ 9: [(R, "2, 2, 6", 2, 1, 1), (R, "2, 2, 8", 2, 1), (R, "2, 2, 2", 2, 1), (T, "2, 2, 2")],
 }
 search = {
  2: ["8, 8, 2", "8, 8, 4", "16, 8, 4", "8, 4, 8", "8, 8, 8", "16, 8, 2"],
@@ -40,10 +41,10 @@ geo = {  # factors on the fly: (tile, Z of all slabs up front)
  3: [("8, 4, 2", 1), ("4, 4, 4", 1)],
  4: [("4, 4, 2", 1), ("4, 4, 4", 1)],
  5: [("4, 2, 2", 1), ("2, 2, 2", 1)],
- 6: [("2, 2, 2", 1), ("4, 2, 2", 0)],
+ 6: [("2, 2, 8", 0), ("2, 2, 2", 1)],
  7: [("2, 2, 2", 0), ("2, 2, 1", 0)],
- 8: [("2, 2, 2", 0), ("2, 2, 1", 0)],
- 9: [("2, 2, 2", 0), ("2, 2, 1", 0)],
+ 8: [("2, 2, 4", 0), ("2, 2, 2", 0)],
+ 9: [("2, 2, 4", 0), ("2, 2, 2", 0)],
 }
 mk = {R: "make_apply3d_f32r", T: "make_apply3d_f32"}
 name = {R: "register prefetch", T: "TMA ring"}
@@ -54,8 +55,9 @@ for P in range(2, 10):
          "// BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:"]
     def describe(c):
         v, t = c[0], c[1]
-        return "%s, tile %s%s%s" % (name[v], t, (", registers capped for %d resident blocks" % c[2]) if len(c) > 2 and c[2] else "",
-                                   ", tables reloaded for the transposed sweep" if len(c) > 3 and c[3] else "")
+        return "%s, tile %s%s%s%s" % (name[v], t, (", registers capped for %d resident blocks" % c[2]) if len(c) > 2 and c[2] else "",
+                                     ", tables reloaded for the transposed sweep" if len(c) > 3 and c[3] else "",
+                                     " (BF16 too)" if len(c) > 4 and c[4] else "")
     for c in main[P]:
         if c[0] == "pair":
             L.append("//   FP32: %s; BF16: %s" % (describe(c[1]), describe(c[2])))
@@ -74,9 +76,12 @@ for P in range(2, 10):
         v, t = c[0], c[1]
         minb = c[2] if len(c) > 2 else 0
         rl = "true" if len(c) > 3 and c[3] else "false"
+        if v == R and (minb or rl == "true") and len(c) > 4 and c[4]:
+            return ("%s<%d, %s, true, 2, %d, %s>()" % (mk[v], P, t, minb, rl),
+                    "%s<%d, %s, false, 2, %d, %s>()" % (mk[v], P, t, minb, rl))
         if v == R and (minb or rl == "true"):
             # BF16 keeps the compiler's register choice and the tables in registers
-            # (both measured faster for the bfloat16 stream)
+            # (measured faster for the bfloat16 stream at these orders)
             return ("%s<%d, %s, true>()" % (mk[v], P, t),
                     "%s<%d, %s, false, 2, %d, %s>()" % (mk[v], P, t, minb, rl))
         if v == T and rl == "true":
