@@ -379,26 +379,51 @@ cudaError_t launch_export_factors(const FactorLayout &L, int op, int64_t Qtot, c
 // The tiles containing dof index i of one direction are t*S <= i <= t*S + E - 1,
 // 0 <= t < T; per direction a table gives, for every i, the first such tile
 // (.x) and (number of tiles << 16) | (i's local index in the first tile) (.y),
-// built on the host at setup (gather_table), so the kernel does no division.
+// built on the host at setup (gather_table), so the kernel does no per-tile
+// division. The tables are constant, so they are read before the wait for the
+// tile kernel's results.
+//
+// TWO (at most two tiles per direction contain a dof): a thread owns one
+// (i0, i1) of the flattened first two directions (one division by N0), so no
+// thread idles on short rows; its <= 8 loads are predicated, not looped.
+// Otherwise a block covers 128 consecutive i0 of one row (i1, i2 from the
+// grid), so the threads of a warp share the per-row tile counts of their loops.
 template <typename T, bool TWO>
 __global__ void gather_kernel(const T *__restrict__ vpart, T *__restrict__ v, const int2 *__restrict__ g0,
                               const int2 *__restrict__ g1, const int2 *__restrict__ g2, int N0, int N1,
                               int N2, int T0, int T1, int S0, int S1, int S2, int E0, int E1, int vol) {
+  const int N01 = N0 * N1;
+  int i0, i1;
+  bool active;
+  if (TWO) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    active = n < N01;
+    i1 = active ? n / N0 : 0;
+    i0 = n - i1 * N0;
+  } else {
+    i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    i1 = blockIdx.y;
+    active = i0 < N0;
+  }
+  const int z0 = TWO ? blockIdx.y : blockIdx.z, zstep = TWO ? gridDim.y : gridDim.z;
+  int2 a0 = make_int2(0, 0), a1 = make_int2(0, 0), a2z = make_int2(0, 0);
+  if (active) {
+    a0 = g0[i0];
+    if (i1 < N1) a1 = g1[i1];
+    if (z0 < N2) a2z = g2[z0];
+  }
   pdl_wait_primary();
-  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i0 >= N0) return;
-  const int2 a0 = g0[i0];
+  if (!active) return;
   const int c0 = a0.y >> 16, l0 = a0.y & 0xffff;
-  for (int i2 = blockIdx.z; i2 < N2; i2 += gridDim.z) {
-    const int2 a2 = g2[i2];
-    const int c2 = a2.y >> 16, l2 = a2.y & 0xffff;
-    for (int i1 = blockIdx.y; i1 < N1; i1 += gridDim.y) {
-      const int2 a1 = g1[i1];
-      const int c1 = a1.y >> 16, l1 = a1.y & 0xffff;
+  for (; i1 < N1; i1 += TWO ? N1 : gridDim.y) {
+    if (!TWO && i1 != (int)blockIdx.y) a1 = g1[i1];
+    const int c1 = a1.y >> 16, l1 = a1.y & 0xffff;
+    for (int i2 = z0; i2 < N2; i2 += zstep) {
+      const int2 a2 = i2 == z0 ? a2z : g2[i2];
+      const int c2 = a2.y >> 16, l2 = a2.y & 0xffff;
       T acc = T(0);
       if (TWO) {
-        // at most two tiles per direction: all loads first, then the sums in
-        // tile order (t2, t1, t0 ascending)
+        // all loads first, then the sums in tile order (t2, t1, t0 ascending)
         T x[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -421,7 +446,7 @@ __global__ void gather_kernel(const T *__restrict__ vpart, T *__restrict__ v, co
               acc += vpart[tile * vol + loc];
             }
       }
-      v[((int64_t)i2 * N1 + i1) * N0 + i0] = acc;
+      v[(int64_t)i2 * N01 + (int64_t)i1 * N0 + i0] = acc;
     }
   }
 }
@@ -452,7 +477,10 @@ cudaError_t launch_gather(int d, int float_vectors, const void *vpart, void *v, 
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.gridDim = dim3((N[0] + 127) / 128, std::min(N1, 65535), std::min(N2, 65535));
+  if (two)
+    cfg.gridDim = dim3((N[0] * N1 - 1) / 128 + 1, std::min(N2, 65535), 1);
+  else
+    cfg.gridDim = dim3((N[0] + 127) / 128, std::min(N1, 65535), std::min(N2, 65535));
   cfg.blockDim = dim3(128);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
