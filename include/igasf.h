@@ -98,7 +98,11 @@ typedef struct {
                             honoured only where a kernel is built for that shape */
   int kernel_variant;    /* IGASF_KERNEL_*, 0 = the library's choice */
   int geometry;          /* IGASF_GEOMETRY_*, 0 = stored factors */
-  int reserved[6];       /* must be zero */
+  int deterministic;     /* 0 (default) or 1: applies are bitwise reproducible from run to
+                            run. This is the only mode built: the gather sums the <= 2^d tile
+                            contributions of each dof in a fixed order and no kernel uses
+                            floating-point atomics. Other values: IGASF_ERR_INVALID_ARG */
+  int reserved[5];       /* must be zero */
 } igasf_options;
 
 /* Where the FP32 apply gets the factors w F.
@@ -215,6 +219,19 @@ int igasf_get_tables(igasf_handle h, int dir, double *nodes, double *weights, do
 int igasf_get_factors(igasf_handle h, int op, int prec, double *out);
 
 /*
+ * The physical quadrature points G(x_q) (Sec. 6.2: G = sum_n c_n phi_n,
+ * evaluated by the same sum factorization as the factors, in FP64 on the
+ * device), for callers that evaluate a coefficient on the physical domain
+ * (Example 1: A lives on Omega and is pulled back through G) and pass it per
+ * quadrature point with IGASF_COEF_VALUES. Host output xyz_host of
+ * num_quad_points * d doubles: point q (lexicographic, first index fastest,
+ * the order IGASF_COEF_VALUES expects) at xyz_host[q*d .. q*d + d - 1].
+ * Synchronous; allocates a temporary device buffer of the output's size.
+ * Errors: INVALID_ARG, CUDA, OOM.
+ */
+int igasf_quad_points(igasf_handle h, double *xyz_host);
+
+/*
  * Per-kernel timing with CUDA events, for benchmarks. igasf_profile_begin
  * creates events for up to `max_applies` later applies on this handle; each of
  * those applies then records an event before its tile kernel, between the tile
@@ -238,11 +255,14 @@ int igasf_profile_end(igasf_handle h, double *ms, int *applies);
 int igasf_device_status(igasf_handle h, int clear);
 
 /*
- * Test hook for the bounded waits: from now on, tile 0 of every FP32/BF16 3D apply
- * on this handle never receives factor slab `skip_slab` (-1 turns this off),
- * and every wait gives up after `wait_limit_cycles` clock cycles (default 2e9,
- * about one second; minimum 1000). Results of applies made while a slab is
- * skipped are invalid. Errors: INVALID_ARG.
+ * Test hook for the bounded waits: from now on, in every FP32/BF16 3D apply on
+ * this handle whose tile kernel streams its factors by bulk copies
+ * (IGASF_KERNEL_RING), tile 0 never receives factor slab `skip_slab` nor any
+ * later slab (its producer stops issuing copies there, after waiting for the
+ * ones already issued; -1 turns this off), and every wait gives up after
+ * `wait_limit_cycles` clock cycles (default 2e9, about one second; minimum
+ * 1000). Results of applies made while slabs are withheld are invalid.
+ * Errors: INVALID_ARG.
  */
 int igasf_set_test_fault(igasf_handle h, int skip_slab, long long wait_limit_cycles);
 
@@ -252,18 +272,21 @@ int igasf_set_test_fault(igasf_handle h, int skip_slab, long long wait_limit_cyc
  * for instance code that hands all device memory to its own arena and forbids
  * further cudaMalloc/cudaFree calls (both can synchronize the whole device).
  *
- * It computes the same v = A u with the same kernels, but its per-tile scratch
+ * It computes the same v = A u with the same kernels, in the same order, so
+ * its result equals igasf_apply_prec's bit for bit; but its per-tile scratch
  * (the partial results that the gather sums) lives in one static device array
- * of IGASF_NOALLOC_SCRATCH_BYTES that the library reserves on every GPU where it
- * is loaded, for the life of the process; it does not use the plan's own
- * workspace and allocates nothing. Plans whose scratch need exceeds that size
- * (igasf_describe().workspace_bytes) are rejected with IGASF_ERR_UNSUPPORTED.
- * The first call on each device looks up the array's device address (with that
- * device current) and must therefore come before any stream capture. All calls
- * on a device share the array: calls whose kernels may run at the same time on
- * the GPU race and give wrong results, so order them (one stream). The array
- * keeps the last call's contents; nothing in it needs to start at zero.
- * Arguments, ordering and errors are otherwise those of igasf_apply_prec.
+ * of IGASF_NOALLOC_SCRATCH_BYTES instead of the plan's own workspace, and it
+ * allocates nothing. The array is reserved on a device when the library's
+ * module holding it is loaded there, which igasf_setup forces (it looks the
+ * array's device address up for the plan's device and caches it), and stays
+ * reserved until the process exits. Plans whose scratch need exceeds that
+ * size (igasf_describe().workspace_bytes) are rejected with
+ * IGASF_ERR_UNSUPPORTED; a call with another device current than the plan's
+ * is rejected with IGASF_ERR_INVALID_ARG. All calls on a device share the
+ * array: calls whose kernels may run at the same time on the GPU race and
+ * give wrong results, so order them (one stream). The array keeps the last
+ * call's contents; nothing in it needs to start at zero. Arguments, ordering
+ * and other errors are those of igasf_apply_prec.
  */
 #define IGASF_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 int igasf_apply_noalloc(igasf_handle h, int op, int prec, const void *u, void *v, void *stream);

@@ -61,7 +61,11 @@ def _load():
         lib.orc_apply_rows.argtypes = patch_args + [ctypes.c_int, _dp, ctypes.c_int64, _lp, _dp,
                                                     _dp, ctypes.c_int]
         lib.orc_apply_elementwise.argtypes = patch_args + [ctypes.c_int, _dp, _dp]
+        lib.orc_apply_qp.argtypes = patch_args + [ctypes.c_int, _dp, _dp, ctypes.c_int]
+        lib.orc_assemble_rows.argtypes = patch_args + [ctypes.c_int, ctypes.c_int64, _lp, _lp, _lp,
+                                                       _dp, ctypes.c_int]
         lib.orc_max_threads.argtypes = []
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
         lib.orc_round_significand.argtypes = [ctypes.c_double, ctypes.c_int]
         lib.orc_round_significand.restype = ctypes.c_double
         lib.orc_set_stored_factor_bits.argtypes = [ctypes.c_int]
@@ -198,6 +202,39 @@ def apply_elementwise(patch, op: int, u):
     v = np.zeros(patch.num_dofs)
     _check(_load().orc_apply_elementwise(*pa.args, op, _ptr(u), _ptr(v)))
     return v
+
+
+def apply_qp(patch, op: int, u, threads: int = 0):
+    """Whole v = A u point by point (value or gradient of u at each quadrature
+    point by direct sums, times w F, scattered to the test functions)."""
+    pa = _PatchArgs(patch)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    v = np.zeros(patch.num_dofs)
+    _check(_load().orc_apply_qp(*pa.args, op, _ptr(u), _ptr(v), int(threads)))
+    return v
+
+
+def assemble_rows(patch, op: int, rows: Sequence[int], threads: int = 0):
+    """CSR (rowptr, colind, val) of the selected rows of A, each row from the
+    definition; row i of the result is row rows[i] of A."""
+    pa = _PatchArgs(patch)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    rowptr = np.zeros(len(rows) + 1, dtype=np.int64)
+    lib = _load()
+    _check(lib.orc_assemble_rows(*pa.args, op, len(rows), _ptr(rows, _lp), _ptr(rowptr, _lp),
+                                 _ptr(None, _lp), _ptr(None), int(threads)))
+    nz = int(rowptr[-1])
+    colind = np.zeros(nz, dtype=np.int64)
+    val = np.zeros(nz)
+    _check(lib.orc_assemble_rows(*pa.args, op, len(rows), _ptr(rows, _lp), _ptr(rowptr, _lp),
+                                 _ptr(colind, _lp), _ptr(val), int(threads)))
+    return rowptr, colind, val
+
+
+def set_threads(n: int):
+    """Number of OpenMP threads of later oracle calls that take no `threads`
+    argument (the CSR product)."""
+    _check(_load().orc_set_threads(int(n)))
 
 
 def max_threads() -> int:

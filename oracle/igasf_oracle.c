@@ -28,8 +28,10 @@
  *     lexicographic order pi, first index fastest (Sec. 3.1);
  *   - tensor-product quadrature X = X_1 x ... x X_d, w = prod w_delta (Sec. 3.1).
  *
- * Build: gcc -O2 -fPIC -shared -fopenmp (OpenMP is used only to run
- * independent rows of the row-sampled apply on several cores).
+ * Build: gcc -O2 -fPIC -shared -fopenmp (OpenMP runs independent pieces on
+ * several cores: the rows of the row-wise apply and assembly, the rows of the
+ * CSR product, and race-free classes of element layers of the point-by-point
+ * apply; no piece's arithmetic depends on the thread count).
  */
 #include <math.h>
 #include <stdint.h>
@@ -582,15 +584,76 @@ int orc_assemble_csr(PATCH_ARGS, int op, int64_t *rowptr, int64_t *colind, doubl
   return ORC_OK;
 }
 
-/* y = A x for a CSR matrix. */
+/* y = A x for a CSR matrix, rows spread over the OpenMP threads (each row is
+ * summed in column order by one thread, so the result does not depend on the
+ * thread count). */
 int orc_spmv(int64_t nrows, const int64_t *rowptr, const int64_t *colind, const double *val,
              const double *x, double *y) {
+#pragma omp parallel for schedule(static)
   for (int64_t r = 0; r < nrows; ++r) {
     double s = 0.0;
     for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) s += val[k] * x[colind[k]];
     y[r] = s;
   }
   return ORC_OK;
+}
+
+/* The entries A_mn of one row m (per-direction indices m[]) for every n in the
+ * window |n_a - m_a| <= p_a - 1, each summed from the definition over the
+ * quadrature points of the elements in the support of phi_m, into
+ * loc[sum_a (n_a - m_a + p_a - 1) prod_{b<a} W_b], W_a = 2 p_a - 1 (entries
+ * with n outside the patch stay zero). */
+static void row_window(const orc_patch *P, const int *m, int op, const int *W, double *loc) {
+  const int d = P->d;
+  int pe[ORC_MAXD] = {1, 1, 1};
+  for (int a = 0; a < d; ++a) pe[a] = P->p[a];
+  memset(loc, 0, sizeof(double) * (size_t)W[0] * W[1] * W[2]);
+  /* elements in the support of phi_m: spans k in [m_a, m_a + p_a - 1] */
+  int elo[ORC_MAXD] = {0, 0, 0}, ehi[ORC_MAXD] = {0, 0, 0};
+  for (int a = 0; a < d; ++a) { elo[a] = m[a]; ehi[a] = m[a] + P->p[a] - 1; }
+  for (int k3 = elo[2]; k3 <= ehi[2]; ++k3)
+    for (int k2 = elo[1]; k2 <= ehi[1]; ++k2)
+      for (int k1 = elo[0]; k1 <= ehi[0]; ++k1) {
+        int k[ORC_MAXD] = {k1, k2, k3};
+        int e[ORC_MAXD] = {0, 0, 0}, f[ORC_MAXD] = {0, 0, 0}, ok = 1;
+        for (int a = 0; a < d; ++a) {
+          if (k[a] < 0 || k[a] >= P->nk[a] || P->elem_of_span[a][k[a]] < 0) { ok = 0; break; }
+          e[a] = P->elem_of_span[a][k[a]];
+          f[a] = first_active(P, a, e[a]);
+        }
+        if (!ok) continue;
+        for (int g3 = 0; g3 < pe[2]; ++g3)
+          for (int g2 = 0; g2 < pe[1]; ++g2)
+            for (int g1 = 0; g1 < pe[0]; ++g1) {
+              int q[ORC_MAXD] = {e[0] * pe[0] + g1, e[1] * pe[1] + g2, e[2] * pe[2] + g3};
+              orc_qp g;
+              eval_qp(P, q, &g);
+              for (int j3 = 0; j3 < pe[2]; ++j3)
+                for (int j2 = 0; j2 < pe[1]; ++j2)
+                  for (int j1 = 0; j1 < pe[0]; ++j1) {
+                    int n[ORC_MAXD] = {f[0] + j1, d > 1 ? f[1] + j2 : 0, d > 2 ? f[2] + j3 : 0};
+                    int64_t widx = 0, s = 1;
+                    for (int a = 0; a < d; ++a) {
+                      widx += s * (n[a] - m[a] + P->p[a] - 1);
+                      s *= W[a];
+                    }
+                    loc[widx] += integrand(P, &g, q, m, n, op);
+                  }
+            }
+      }
+}
+
+/* Column n of window entry widx of row m; 0 if n lies outside the patch. */
+static int window_col(const orc_patch *P, const int *m, const int *W, int64_t widx, int64_t *col) {
+  int n[ORC_MAXD] = {0, 0, 0};
+  int64_t r = widx;
+  for (int a = 0; a < P->d; ++a) {
+    n[a] = (int)(r % W[a]) + m[a] - P->p[a] + 1;
+    r /= W[a];
+    if (n[a] < 0 || n[a] >= P->N[a]) return 0;
+  }
+  *col = lin(P, n);
+  return 1;
 }
 
 /* Selected rows of v = A u, each row assembled on its own from the definition:
@@ -608,9 +671,8 @@ int orc_apply_rows(PATCH_ARGS, int op, const double *u, int64_t nrows, const int
 #else
   (void)threads;
 #endif
-  int pe[ORC_MAXD] = {1, 1, 1};
   int W[ORC_MAXD] = {1, 1, 1};      /* width of the local column window, 2p - 1 */
-  for (int a = 0; a < d; ++a) { pe[a] = P.p[a]; W[a] = 2 * P.p[a] - 1; }
+  for (int a = 0; a < d; ++a) W[a] = 2 * P.p[a] - 1;
   int64_t wsize = (int64_t)W[0] * W[1] * W[2];
 #pragma omp parallel
   {
@@ -619,55 +681,71 @@ int orc_apply_rows(PATCH_ARGS, int op, const double *u, int64_t nrows, const int
     for (int64_t ir = 0; ir < nrows; ++ir) {
       int m[ORC_MAXD] = {0, 0, 0};
       unlin(&P, rows[ir], m);
-      memset(loc, 0, sizeof(double) * (size_t)wsize);
-      /* elements in the support of phi_m: spans k in [m_a, m_a + p_a - 1] */
-      int elo[ORC_MAXD] = {0, 0, 0}, ehi[ORC_MAXD] = {0, 0, 0};
-      for (int a = 0; a < d; ++a) { elo[a] = m[a]; ehi[a] = m[a] + P.p[a] - 1; }
-      for (int k3 = elo[2]; k3 <= ehi[2]; ++k3)
-        for (int k2 = elo[1]; k2 <= ehi[1]; ++k2)
-          for (int k1 = elo[0]; k1 <= ehi[0]; ++k1) {
-            int k[ORC_MAXD] = {k1, k2, k3};
-            int e[ORC_MAXD] = {0, 0, 0}, f[ORC_MAXD] = {0, 0, 0}, ok = 1;
-            for (int a = 0; a < d; ++a) {
-              if (k[a] < 0 || k[a] >= P.nk[a] || P.elem_of_span[a][k[a]] < 0) { ok = 0; break; }
-              e[a] = P.elem_of_span[a][k[a]];
-              f[a] = first_active(&P, a, e[a]);
-            }
-            if (!ok) continue;
-            for (int g3 = 0; g3 < pe[2]; ++g3)
-              for (int g2 = 0; g2 < pe[1]; ++g2)
-                for (int g1 = 0; g1 < pe[0]; ++g1) {
-                  int q[ORC_MAXD] = {e[0] * pe[0] + g1, e[1] * pe[1] + g2, e[2] * pe[2] + g3};
-                  orc_qp g;
-                  eval_qp(&P, q, &g);
-                  for (int j3 = 0; j3 < pe[2]; ++j3)
-                    for (int j2 = 0; j2 < pe[1]; ++j2)
-                      for (int j1 = 0; j1 < pe[0]; ++j1) {
-                        int n[ORC_MAXD] = {f[0] + j1, d > 1 ? f[1] + j2 : 0, d > 2 ? f[2] + j3 : 0};
-                        int64_t widx = 0, s = 1;
-                        for (int a = 0; a < d; ++a) {
-                          widx += s * (n[a] - m[a] + P.p[a] - 1);
-                          s *= W[a];
-                        }
-                        loc[widx] += integrand(&P, &g, q, m, n, op);
-                      }
-                }
-          }
+      row_window(&P, m, op, W, loc);
       double sum = 0.0, sabs = 0.0;
       for (int64_t widx = 0; widx < wsize; ++widx) {
-        int n[ORC_MAXD] = {0, 0, 0};
-        int64_t r = widx, ok = 1;
-        for (int a = 0; a < d; ++a) {
-          n[a] = (int)(r % W[a]) + m[a] - P.p[a] + 1;
-          r /= W[a];
-          if (n[a] < 0 || n[a] >= P.N[a]) ok = 0;
-        }
-        if (!ok) continue;
-        sum += loc[widx] * u[lin(&P, n)];
+        int64_t col;
+        if (!window_col(&P, m, W, widx, &col)) continue;
+        sum += loc[widx] * u[col];
         sabs += fabs(loc[widx]);
       }
       v[ir] = sum;
       if (rowabs) rowabs[ir] = sabs;
+    }
+    free(loc);
+  }
+  patch_free(&P);
+  return ORC_OK;
+}
+
+/* CSR of selected rows of A, each row assembled on its own from the definition
+ * (as in orc_apply_rows): row ir of the output holds A_{rows[ir], n} for every
+ * n with |n_a - m_a| <= p_a - 1 inside the patch (the support pattern of the
+ * nnz Corollary, Sec. 3.2), columns ascending. Call with colind == NULL to get
+ * rowptr (nrows + 1 entries) only; then again with colind and val of rowptr[nrows]
+ * entries. Rows run on `threads` OpenMP threads (0 = the runtime default). */
+int orc_assemble_rows(PATCH_ARGS, int op, int64_t nrows, const int64_t *rows, int64_t *rowptr,
+                      int64_t *colind, double *val, int threads) {
+  orc_patch P;
+  int rc = patch_build(&P, PATCH_PASS);
+  if (rc) { patch_free(&P); return rc; }
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#else
+  (void)threads;
+#endif
+  int W[ORC_MAXD] = {1, 1, 1};
+  for (int a = 0; a < d; ++a) W[a] = 2 * P.p[a] - 1;
+  int64_t wsize = (int64_t)W[0] * W[1] * W[2];
+  if (!colind) {
+    rowptr[0] = 0;
+    for (int64_t ir = 0; ir < nrows; ++ir) {
+      int m[ORC_MAXD] = {0, 0, 0};
+      unlin(&P, rows[ir], m);
+      int64_t cnt = 0, col;
+      for (int64_t widx = 0; widx < wsize; ++widx) cnt += window_col(&P, m, W, widx, &col);
+      rowptr[ir + 1] = rowptr[ir] + cnt;
+    }
+    patch_free(&P);
+    return ORC_OK;
+  }
+#pragma omp parallel
+  {
+    double *loc = (double *)malloc(sizeof(double) * (size_t)wsize);
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t ir = 0; ir < nrows; ++ir) {
+      int m[ORC_MAXD] = {0, 0, 0};
+      unlin(&P, rows[ir], m);
+      row_window(&P, m, op, W, loc);
+      int64_t pos = rowptr[ir], col;
+      /* window index order is lexicographic in n with the first index
+         fastest, i.e. ascending global column */
+      for (int64_t widx = 0; widx < wsize; ++widx) {
+        if (!window_col(&P, m, W, widx, &col)) continue;
+        colind[pos] = col;
+        val[pos] = loc[widx];
+        ++pos;
+      }
     }
     free(loc);
   }
@@ -722,6 +800,101 @@ int orc_apply_elementwise(PATCH_ARGS, int op, const double *u, double *v) {
   }
   free(Ae);
   patch_free(&P);
+  return ORC_OK;
+}
+
+/* Whole v = A u point by point, without a matrix: for every element and every
+ * one of its quadrature points x, first the value of u at x (mass) or its
+ * partial derivatives d u / d xi_j (stiffness), each by the direct sum over
+ * the p^d functions active on the element (every basis value the full tensor
+ * product, as in basis_at: no sum factorization); then the weighted factor
+ * times that, g = w F(x) d^theta u(x); then v_m += d^eta phi_m(x) g for every
+ * active test function m. Summed over all points this is
+ * v_m = sum_n sum_x w F d^theta phi_n d^eta phi_m u_n = (A u)_m, the definition
+ * (eq. quadrature:1) with the sum over n taken first, i.e. the local matrix
+ * B_e^T D_e B_e applied to u_e without being formed. Stored-factor rounding
+ * (stored_bits) applies to w F exactly as in integrand().
+ * Parallel without races and in a fixed order: element layers of the last
+ * direction whose indices agree modulo p touch disjoint dof layers, so the
+ * layers of one residue class run in parallel (one thread per layer) and the
+ * classes run one after another; inside a layer elements run in order. */
+int orc_apply_qp(PATCH_ARGS, int op, const double *u, double *v, int threads) {
+  orc_patch P;
+  int rc = patch_build(&P, PATCH_PASS);
+  if (rc) { patch_free(&P); return rc; }
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#else
+  (void)threads;
+#endif
+  int Ke[ORC_MAXD] = {1, 1, 1}, pe[ORC_MAXD] = {1, 1, 1};
+  for (int a = 0; a < d; ++a) { Ke[a] = P.K[a]; pe[a] = P.p[a]; }
+  const int last = d - 1;
+  const int nloc = pe[0] * pe[1] * pe[2];
+  memset(v, 0, sizeof(double) * (size_t)P.Ntot);
+  for (int cls = 0; cls < pe[last]; ++cls) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int layer = cls; layer < Ke[last]; layer += pe[last]) {
+      int elo[ORC_MAXD] = {0, 0, 0}, ehi[ORC_MAXD] = {1, 1, 1};
+      for (int a = 0; a < d; ++a) { elo[a] = 0; ehi[a] = Ke[a]; }
+      elo[last] = layer;
+      ehi[last] = layer + 1;
+      for (int e3 = elo[2]; e3 < ehi[2]; ++e3)
+        for (int e2 = elo[1]; e2 < ehi[1]; ++e2)
+          for (int e1 = elo[0]; e1 < ehi[0]; ++e1) {
+            int e[ORC_MAXD] = {e1, e2, e3}, f[ORC_MAXD] = {0, 0, 0};
+            for (int a = 0; a < d; ++a) f[a] = first_active(&P, a, e[a]);
+            for (int g3 = 0; g3 < pe[2]; ++g3)
+              for (int g2 = 0; g2 < pe[1]; ++g2)
+                for (int g1 = 0; g1 < pe[0]; ++g1) {
+                  int q[ORC_MAXD] = {e[0] * pe[0] + g1, e[1] * pe[1] + g2, e[2] * pe[2] + g3};
+                  orc_qp g;
+                  eval_qp(&P, q, &g);
+                  /* d^theta u at x: value, or reference partial derivatives */
+                  double du[ORC_MAXD] = {0.0, 0.0, 0.0}, uval = 0.0;
+                  for (int in = 0; in < nloc; ++in) {
+                    int n[ORC_MAXD] = {f[0] + in % pe[0], f[1] + (in / pe[0]) % pe[1],
+                                       f[2] + in / (pe[0] * pe[1])};
+                    double un = u[lin(&P, n)];
+                    if (op == ORC_MASS) uval += basis_at(&P, q, n, -1) * un;
+                    else for (int j = 0; j < d; ++j) du[j] += basis_at(&P, q, n, j) * un;
+                  }
+                  /* g = w F d^theta u */
+                  double gm = 0.0, gk[ORC_MAXD] = {0.0, 0.0, 0.0};
+                  if (op == ORC_MASS) {
+                    double wf = g.w * g.FM;
+                    if (stored_bits > 0) wf = orc_round_significand(wf, stored_bits);
+                    gm = wf * uval;
+                  } else {
+                    for (int i = 0; i < d; ++i)
+                      for (int j = 0; j < d; ++j) {
+                        double wf = g.w * g.FK[i][j];
+                        if (stored_bits > 0) wf = orc_round_significand(wf, stored_bits);
+                        gk[i] += wf * du[j];
+                      }
+                  }
+                  /* v_m += d^eta phi_m g */
+                  for (int im = 0; im < nloc; ++im) {
+                    int m[ORC_MAXD] = {f[0] + im % pe[0], f[1] + (im / pe[0]) % pe[1],
+                                       f[2] + im / (pe[0] * pe[1])};
+                    double c = 0.0;
+                    if (op == ORC_MASS) c = basis_at(&P, q, m, -1) * gm;
+                    else for (int i = 0; i < d; ++i) c += basis_at(&P, q, m, i) * gk[i];
+                    v[lin(&P, m)] += c;
+                  }
+                }
+          }
+    }
+  }
+  patch_free(&P);
+  return ORC_OK;
+}
+
+int orc_set_threads(int n) {
+  if (n < 1) return ORC_ERR_ARG;
+#ifdef _OPENMP
+  omp_set_num_threads(n);
+#endif
   return ORC_OK;
 }
 

@@ -307,8 +307,9 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
   if (tid >= NTC) {
     if (tid == NTC) {
       bool bad = false;
-      uint32_t g = 0;
-      for (int tile = first_tile; tile < tile_end; tile += tile_stride) {
+      bool stopped = false;   // the test hook withheld a fill: issue no further copies
+      uint32_t g = 0, issued = 0;
+      for (int tile = first_tile; tile < tile_end && !stopped; tile += tile_stride) {
         const int t3 = tile / (prm.T[0] * prm.T[1]);
         const int nslab = min(S3, prm.K[2] - t3 * S3) * P;
         const unsigned char *src = static_cast<const unsigned char *>(prm.D) + (size_t)tile * Q3 * SB;
@@ -317,16 +318,22 @@ __device__ __forceinline__ void apply3d_f32_body(const ApplyParams &prm, const i
           if (g >= (uint32_t)R &&
               !mbar_wait_bounded(smem_addr(&empty[slot]), ((g / R) - 1) & 1, prm.wait_limit))
             bad = true;
-          if (tile == 0 && s == prm.skip_slab) continue;   // test hook: a fill that never comes
+          if (tile == 0 && s == prm.skip_slab) {   // test hook: a fill that never comes
+            stopped = true;
+            break;
+          }
           mbar_arrive_expect_tx(smem_addr(&full[slot]), SB);
           bulk_copy_g2s(smem_addr(ring + (size_t)slot * SB), src + (size_t)s * SB, SB,
                         smem_addr(&full[slot]));
+          issued = g + 1;
         }
       }
-      // leave no copy in flight: wait for the last fill of every slot used
-      const uint32_t used = g < (uint32_t)R ? g : (uint32_t)R;
+      // leave no copy in flight: wait for the last fill of every slot used.
+      // Every fill issued completes the phase it was issued for (fills stop at
+      // the first withheld one), so these waits see the copies land.
+      const uint32_t used = issued < (uint32_t)R ? issued : (uint32_t)R;
       for (uint32_t k = 0; k < used; ++k) {
-        const uint32_t gi = g - 1 - k;
+        const uint32_t gi = issued - 1 - k;
         if (!mbar_wait_bounded(smem_addr(&full[gi % R]), (gi / R) & 1, prm.wait_limit)) bad = true;
       }
       if (bad) atomicOr(prm.status, 1u);

@@ -45,6 +45,7 @@ void free_plan(igasf_plan *h) {
   if (!h) return;
   destroy_events(h);
   cudaFree(h->status);
+  cudaFree(h->ctrl64);
   cudaFree(h->dinv64);
   cudaFree(h->dinv32);
   for (int a = 0; a < kMaxDim; ++a) {
@@ -252,6 +253,8 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     return fail(IGASF_ERR_INVALID_ARG, "options.precisions must include default_prec");
   if (o.geometry != IGASF_GEOMETRY_STORED && o.geometry != IGASF_GEOMETRY_ON_THE_FLY)
     return fail(IGASF_ERR_INVALID_ARG, "options.geometry = %d", o.geometry);
+  if (o.deterministic != 0 && o.deterministic != 1)
+    return fail(IGASF_ERR_INVALID_ARG, "options.deterministic = %d (0 or 1)", o.deterministic);
   const bool geo = o.geometry == IGASF_GEOMETRY_ON_THE_FLY;
   if (geo && !(precs & IGASF_PREC_BIT(IGASF_FP32)))
     return fail(IGASF_ERR_INVALID_ARG, "factors on the fly are an FP32 mode: store FP32");
@@ -411,12 +414,12 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     TRY_CUDA(v.k.prepare(), "kernel attributes");
     if (!v.on_the_fly) g.out[g.nout++] = v.L;
   }
-  // geometry factors
-  double *ctrl_d = nullptr, *coef_d = nullptr;
+  // geometry factors (the FP64 control points stay on the device for igasf_quad_points)
+  double *coef_d = nullptr;
   unsigned int *bad_d = nullptr;
-  TRY(alloc((void **)&ctrl_d, sizeof(double) * h->Ntot * d, "control points"));
+  TRY(alloc((void **)&h->ctrl64, sizeof(double) * h->Ntot * d, "control points"));
+  double *ctrl_d = h->ctrl64;
   auto cleanup_tmp = [&]() {
-    cudaFree(ctrl_d);
     cudaFree(coef_d);
     cudaFree(bad_d);
   };
@@ -462,6 +465,9 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     free_plan(h);
     return fail(IGASF_ERR_GEOMETRY, "det J <= 0 at some quadrature point: G is not orientation preserving");
   }
+  // locate the static scratch of igasf_apply_noalloc on this device now, so
+  // that its first call allocates nothing (noalloc.cu)
+  noalloc_prepare(h->device);
   *out = h;
   return IGASF_OK;
 }
@@ -650,6 +656,41 @@ int igasf_get_tables(igasf_handle h, int dir, double *nodes, double *weights, do
       for (int j = 0; j < p; ++j) dst[(size_t)q * p + j] = tmp[(size_t)j * Q + q];
   }
   if (e != cudaSuccess) return cuda_fail(e, "copy tables");
+  return IGASF_OK;
+}
+
+int igasf_quad_points(igasf_handle h, double *xyz_host) {
+  if (!h || !xyz_host) return fail(IGASF_ERR_INVALID_ARG, "handle or xyz_host is NULL");
+  GeometryParams g;
+  memset(&g, 0, sizeof(g));
+  g.d = h->d;
+  g.p = h->p;
+  for (int a = 0; a < kMaxDim; ++a) {
+    g.N[a] = h->N[a];
+    g.K[a] = h->K[a];
+    g.tabB[a] = h->tabB[a];
+    g.tabD[a] = h->tabD[a];
+    g.wq[a] = h->weights[a];
+  }
+  g.ctrl = h->ctrl64;
+  g.coef_kind = IGASF_COEF_CONSTANT;   // points only: no factor is written (nout = 0)
+  g.coef_const = 1.0;
+  g.nout = 0;
+  const size_t bytes = sizeof(double) * (size_t)h->Qtot * h->d;
+  double *tmp = nullptr;
+  unsigned int *bad = nullptr;
+  cudaError_t e = cudaMalloc((void **)&tmp, bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&bad, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) {
+    g.bad_det = bad;
+    g.xq_out = tmp;
+    e = launch_geometry(g, nullptr);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(xyz_host, tmp, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  cudaFree(bad);
+  if (e != cudaSuccess) return cuda_fail(e, "quadrature points");
   return IGASF_OK;
 }
 

@@ -119,6 +119,7 @@ struct GeometryParams {
   FactorLayout out[kNumPrec];
   unsigned int *bad_det;              // set to 1 if det J <= 0 somewhere
   double *min_det;                    // unused if NULL
+  double *xq_out;                     // if not NULL: G(x_q), [Qtot][d] lexicographic
 };
 
 // setup kernels (setup.cu)
@@ -134,5 +135,8 @@ cudaError_t launch_export_factors(const FactorLayout &L, int op, int64_t Qtot, c
 cudaError_t launch_gather(int d, int float_vectors, const void *vpart, void *v, const int *N,
                           const int *T, const int *S, int p, int2 *const *gtab, cudaStream_t s);
 void gather_table(int N, int S, int E, int T, std::vector<int2> &out);
+// Locate the static scratch array of igasf_apply_noalloc on `device` (current)
+// and cache its address (noalloc.cu).
+void noalloc_prepare(int device);
 
 }  // namespace igasf

@@ -42,6 +42,7 @@ struct igasf_plan {
   double *weights[igasf::kMaxDim] = {nullptr, nullptr, nullptr};
   double *tabB[igasf::kMaxDim] = {nullptr, nullptr, nullptr};  // FP64 [j][Q]
   double *tabD[igasf::kMaxDim] = {nullptr, nullptr, nullptr};
+  double *ctrl64 = nullptr;              // control points, device, N x d (for igasf_quad_points)
   int default_prec = IGASF_FP64;
   igasf::Variant var[igasf::kNumPrec];
   unsigned int *status = nullptr;        // device status word (bounded waits)

@@ -262,6 +262,8 @@ __global__ void geometry3d_kernel(const GeometryParams g, int Gs, int nb1, int n
       }
       const int qg[3] = {q1g, q2g, q3g};
       write_factors(g, qg, w * adet, dk, 6);
+      if (g.xq_out)
+        for (int c = 0; c < 3; ++c) g.xq_out[qlin * 3 + c] = X[c];
     }
   }
 }
@@ -303,6 +305,10 @@ __global__ void geometry2d_kernel(const GeometryParams g) {
   dk[2] = s * (adj[1][0] * adj[1][0] + adj[1][1] * adj[1][1]);
   const int qg[2] = {q1g, q2g};
   write_factors(g, qg, w * adet, dk, 3);
+  if (g.xq_out) {
+    g.xq_out[q * 2] = X[0];
+    g.xq_out[q * 2 + 1] = X[1];
+  }
 }
 
 int geometry_block_elems(int p) {

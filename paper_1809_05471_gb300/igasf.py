@@ -42,7 +42,7 @@ ERRORS = {
 EXPORTED = [
     "igasf_setup", "igasf_apply", "igasf_apply_prec", "igasf_apply_host", "igasf_destroy",
     "igasf_num_dofs", "igasf_num_quad_points", "igasf_describe", "igasf_get_tables",
-    "igasf_get_factors", "igasf_profile_begin", "igasf_profile_end", "igasf_apply_noalloc",
+    "igasf_get_factors", "igasf_quad_points", "igasf_profile_begin", "igasf_profile_end", "igasf_apply_noalloc",
     "igasf_device_status", "igasf_set_test_fault", "igasf_cg_solve",
     "igasf_batch_create", "igasf_batch_apply", "igasf_batch_info", "igasf_batch_destroy",
     "igasf_autotune", "igasf_list_kernels", "igasf_assembled_nnz", "igasf_assemble_csr",
@@ -64,7 +64,8 @@ class Coef(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precisions", ctypes.c_uint), ("default_prec", ctypes.c_int),
                 ("tile", ctypes.c_int * 3), ("kernel_variant", ctypes.c_int),
-                ("geometry", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("geometry", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class CgReport(ctypes.Structure):
@@ -108,6 +109,7 @@ def load_library(path: str = LIB_PATH):
     lib.igasf_describe.argtypes = [vp, ctypes.c_int, ctypes.POINTER(PlanDesc)]
     lib.igasf_get_tables.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp]
     lib.igasf_get_factors.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
+    lib.igasf_quad_points.argtypes = [vp, dp]
     lib.igasf_apply_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     lib.igasf_cg_solve.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int, ctypes.POINTER(CgReport), vp]
@@ -252,6 +254,12 @@ class Plan:
         _check(load_library().igasf_get_tables(self._h(), direction, _dptr(nodes), _dptr(weights),
                                                _dptr(B), _dptr(dB)))
         return nodes, weights, B, dB
+
+    def quad_points(self) -> np.ndarray:
+        """Physical quadrature points G(x_q), (num_quad_points, d), lexicographic."""
+        out = np.zeros((self.num_quad_points, self.d))
+        _check(load_library().igasf_quad_points(self._h(), _dptr(out)))
+        return out
 
     def factors(self, op: int, prec: int = FP64) -> np.ndarray:
         nf = 1 if op == MASS else self.d * (self.d + 1) // 2

@@ -12,6 +12,23 @@ TOL = {G.FP64: 1e-12, G.FP32: 1e-5}
 DTYPE = {G.FP64: "float64", G.FP32: "float32", G.BF16: "float32"}
 
 
+def tol(prec, patch_or_p):
+    """Scaled max-norm bar of an apply against the oracle at order p.
+
+    FP64: 1e-12 (sum factorization reaches the assembled quadrature operator up
+    to rounding, Sec. 1 and Sec. 8).
+    FP32 (and BF16 against the oracle's operator with the same rounded factors,
+    whose arithmetic is FP32 too): the longest accumulation chain of one output
+    has about 6p + 9 terms (three forward sweeps of p terms, the 3-term product
+    with the factors, three transposed sweeps), so first-order rounding gives
+    (6p + 9) 2^-24 relative to the absolute terms; the bar is twice that
+    (2.5e-6 at p = 2, 7.5e-6 at p = 9)."""
+    p = patch_or_p if isinstance(patch_or_p, (int, np.integer)) else int(patch_or_p.orders[0])
+    if prec == G.FP64:
+        return TOL[G.FP64]
+    return 2.0 * (6 * p + 9) * 2.0 ** -24
+
+
 def gpu_apply(plan, op, u, prec):
     import torch
     dt = getattr(torch, DTYPE[prec])

@@ -5,7 +5,7 @@ import pytest
 import oracle as O
 from paper_1809_05471_gb300 import igasf as G
 from paper_1809_05471_gb300 import inputs as I
-from tests.gpu_helpers import TOL, sample_rows, scaled_err
+from tests.gpu_helpers import sample_rows, scaled_err, tol
 
 pytestmark = pytest.mark.gpu
 
@@ -57,7 +57,7 @@ def test_batch_equals_individual_applies(prec):
                 vr, ra = O.apply_rows(pt, O.STIFFNESS, uk, rows)
             a = batch.offsets[k]
             vk = v[a:a + pt.num_dofs].double().cpu().numpy()[rows]
-            assert scaled_err(vk, vr, ra.max(), uk) < TOL[G.FP32 if prec == G.BF16 else prec]
+            assert scaled_err(vk, vr, ra.max(), uk) < tol(prec, pt)
     for plan in plans:
         assert plan.device_status() == 0
         plan.close()

@@ -31,7 +31,14 @@ MUTATIONS = [
     ("stiffness index", "s += dm * g->FK[i][j] * basis_at(P, q, n, j);",
      "s += dm * g->FK[i][j] * basis_at(P, q, n, i);"),
     ("transposed operand in J", "out->J[i][j] += c * dphi;", "out->J[j][i] += c * dphi;"),
-    ("row support window", "ehi[a] = m[a] + P.p[a] - 1;", "ehi[a] = m[a] + P.p[a] - 2;"),
+    ("row support window", "ehi[a] = m[a] + P->p[a] - 1;", "ehi[a] = m[a] + P->p[a] - 2;"),
+    ("point apply: test function derivative direction",
+     "else for (int i = 0; i < d; ++i) c += basis_at(&P, q, m, i) * gk[i];",
+     "else for (int i = 0; i < d; ++i) c += basis_at(&P, q, m, 0) * gk[i];"),
+    ("point apply: transposed factor",
+     "double wf = g.w * g.FK[i][j];", "double wf = g.w * g.FK[j][i] * (i == j ? 1.0 : 0.5);"),
+    ("point apply: a layer class skipped",
+     "for (int cls = 0; cls < pe[last]; ++cls) {", "for (int cls = 1; cls < pe[last]; ++cls) {"),
     ("stored stiffness factor rounded before the weight",
      "orc_round_significand(g->w * g->FK[i][j], stored_bits)",
      "g->w * orc_round_significand(g->FK[i][j], stored_bits)"),
@@ -70,6 +77,9 @@ def _quick_pins():
         vr, _ = O.apply_rows(patch, op, u, rows)
         if not np.max(np.abs(vr - Ab @ u)) < 1e-13 * np.max(np.abs(Ab @ u)):
             failed.append("rows op %d" % op)
+        vq = O.apply_qp(patch, op, u, threads=3)
+        if not np.max(np.abs(vq - Ab @ u)) < 1e-13 * np.max(np.abs(Ab @ u)):
+            failed.append("point apply op %d" % op)
     # bfloat16-stored factors: ties to even, and the rounded quantity is w F
     if not (O.round_significand(1 + 2.0 ** -8, 8) == 1.0
             and O.round_significand(1 + 3 * 2.0 ** -8, 8) == 1 + 2.0 ** -6

@@ -346,6 +346,45 @@ def test_row_and_elementwise_apply_match_spmv(op):
     assert np.max(np.abs(ra - np.add.reduceat(np.abs(va), rp[:-1]))) < 1e-14 * np.max(ra)
 
 
+@pytest.mark.parametrize("d,p,K", [(2, 2, (5, 4)), (2, 4, (4, 3)), (3, 2, (4, 3, 5)),
+                                   (3, 3, (3, 2, 4)), (3, 5, (2, 3, 2))])
+@pytest.mark.parametrize("op", [O.MASS, O.STIFFNESS])
+@pytest.mark.parametrize("bits", [0, O.BF16_BITS])
+def test_point_apply_matches_brute_force_and_is_thread_independent(d, p, K, op, bits):
+    rng = np.random.default_rng(40 + d + p)
+    knots = [I.open_knots_from_breaks(p, np.concatenate(
+        [[0.0], np.cumsum(h := rng.uniform(0.5, 1.5, k)) / h.sum()])) for k in K]
+    patch, u = I.make_patch(d, p, list(K), noise_amp=0.3 / max(K), seed=9, knots=knots,
+                            coef_kind=I.COEF_EXP_SIN_COS, coef_alpha=0.5)
+    rf = None if bits == 0 else (lambda x: np.ldexp(np.round(np.frexp(x)[0] * 256.0),
+                                                    np.frexp(x)[1] - 8))
+    Ab = brute.dense_operator(patch, op, round_factor=rf)
+    with O.stored_factor_bits(bits):
+        v1 = O.apply_qp(patch, op, u, threads=1)
+        v4 = O.apply_qp(patch, op, u, threads=4)
+    ref = Ab @ u
+    assert np.max(np.abs(v1 - ref)) < 1e-13 * np.max(np.abs(Ab)) * np.max(np.abs(u))
+    assert np.array_equal(v1, v4)
+
+
+@pytest.mark.parametrize("op", [O.MASS, O.STIFFNESS])
+def test_assembled_rows_match_csr(op):
+    patch, u = I.make_patch(3, 3, [4, 3, 5], noise_amp=0.05, seed=6,
+                            coef_kind=I.COEF_EXP_SIN_COS, coef_alpha=0.5)
+    rp, ci, va = O.assemble_csr(patch, op)
+    rows = np.array([0, 7, 31, 32, 33, patch.num_dofs - 1], dtype=np.int64)
+    srp, sci, sva = O.assemble_rows(patch, op, rows, threads=3)
+    s = np.max(np.abs(va))
+    for i, r in enumerate(rows):
+        a, b = rp[r], rp[r + 1]
+        assert np.array_equal(sci[srp[i]:srp[i + 1]], ci[a:b])      # the Corollary's pattern
+        assert np.max(np.abs(sva[srp[i]:srp[i + 1]] - va[a:b])) < 1e-14 * s
+    # the product of the sampled rows is the sampled rows of the product
+    O.set_threads(2)
+    y = O.spmv(srp, sci, sva, u)
+    assert np.max(np.abs(y - O.spmv(rp, ci, va, u)[rows])) < 1e-14 * s * np.max(np.abs(u))
+
+
 def test_quad_data_coefficient_at_physical_point():
     patch, _ = I.config_cube(p=3, K=3)
     qd = O.quad_data(patch)
