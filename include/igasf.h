@@ -69,9 +69,26 @@ typedef enum { IGASF_MASS = 0, IGASF_STIFFNESS = 1 } igasf_op;
  * BF16: factors stored in bfloat16 (each rounded once to nearest even, half
  *       the bytes of FP32); tables, vectors (u, v: float) and arithmetic FP32.
  *       The operator applied is the quadrature operator with those rounded
- *       factors: about 2^-9 relative perturbation of every w F, meant for
- *       inner solves and preconditioners. */
-typedef enum { IGASF_FP64 = 0, IGASF_FP32 = 1, IGASF_BF16 = 2 } igasf_prec;
+ *       factors: at most 2^-8 relative perturbation of every w F, meant for
+ *       inner solves and preconditioners.
+ * TF32: FP32 factors, tables and vectors; the direction-3 contractions (the
+ *       last forward sweep and the first transposed sweep, which carry most of
+ *       the multiply-adds at high order) run on the tensor cores with TF32
+ *       operands (the direction-2 results, the products D grad u and the
+ *       direction-3 tables rounded to 11 significant bits) and FP32
+ *       accumulation; all other arithmetic FP32. 3D only.
+ * BF16_MMA: factors stored in bfloat16 as for BF16; the direction-3
+ *       contractions on the tensor cores with bfloat16 operands (8 significant
+ *       bits) and FP32 accumulation; all other arithmetic FP32. 3D only.
+ * The two tensor-core precisions keep their own factor copy (the tile shapes
+ * of their kernels differ from the FP32/BF16 ones). */
+typedef enum {
+  IGASF_FP64 = 0,
+  IGASF_FP32 = 1,
+  IGASF_BF16 = 2,
+  IGASF_TF32 = 3,
+  IGASF_BF16_MMA = 4
+} igasf_prec;
 #define IGASF_PREC_BIT(prec) (1u << (unsigned)(prec))
 
 /* Coefficient a of the stiffness operator (Example 1 with A = a I, evaluated
@@ -117,12 +134,14 @@ typedef struct {
 enum { IGASF_GEOMETRY_STORED = 0, IGASF_GEOMETRY_ON_THE_FLY = 1 };
 
 /* How the FP32 and BF16 3D tile kernels receive their factors (FP64 and 2D
- * kernels have one scheme: per-thread loads). */
+ * kernels have one scheme: per-thread loads), and which family a kernel is. */
 enum {
   IGASF_KERNEL_DEFAULT = 0,
   IGASF_KERNEL_REGISTERS = 1, /* each thread loads its factors into registers, slabs ahead */
   IGASF_KERNEL_RING = 2,      /* bulk copies into a shared-memory ring by a producer warp */
-  IGASF_KERNEL_ON_THE_FLY = 3 /* reported by igasf_describe for IGASF_GEOMETRY_ON_THE_FLY */
+  IGASF_KERNEL_ON_THE_FLY = 3, /* reported by igasf_describe for IGASF_GEOMETRY_ON_THE_FLY */
+  IGASF_KERNEL_MMA = 4        /* direction-3 sweeps on the tensor cores: the kernels of
+                                 IGASF_TF32 and IGASF_BF16_MMA (per-thread factor loads) */
 };
 
 typedef struct igasf_plan *igasf_handle;

@@ -76,8 +76,9 @@ __device__ __forceinline__ float2 widen(uint32_t c) { return bf16x2_to_float2(c)
 // is issued through the read-only path before its first shared-memory store,
 // so the block waits for one round of load latency instead of one per loop
 // trip. Tables of directions 2 and 3 are stored as duplicated pairs {b, b},
-// padded with zeros to PP entries per quadrature point.
-template <int P, int S1, int S2, int S3, int NT, bool STIFF>
+// padded with zeros to PP entries per quadrature point. DIR3 = false skips the
+// direction-3 tables (kernels that stage them in another form).
+template <int P, int S1, int S2, int S3, int NT, bool STIFF, bool DIR3 = true>
 __device__ __forceinline__ void stage_tile_f32(const ApplyParams &prm, const int tid, const int e01,
                                                const int e02, const int e03, float *t1b, float *t1d,
                                                float *t2b, float *t2d, float *t3b, float *t3d,
@@ -86,12 +87,12 @@ __device__ __forceinline__ void stage_tile_f32(const ApplyParams &prm, const int
   constexpr int Q1 = S1 * P, Q2 = S2 * P, Q3 = S3 * P, PP = P + (P & 1);
   constexpr int VOL = E1 * E2 * E3;
   constexpr int A1 = (P * Q1 + NT - 1) / NT, A2 = (PP * Q2 + NT - 1) / NT;
-  constexpr int A3 = (PP * Q3 + NT - 1) / NT, AU = (VOL + NT - 1) / NT;
+  constexpr int A3 = DIR3 ? (PP * Q3 + NT - 1) / NT : 0, AU = (VOL + NT - 1) / NT;
   const float *gb1 = static_cast<const float *>(prm.tabB[0]), *gd1 = static_cast<const float *>(prm.tabD[0]);
   const float *gb2 = static_cast<const float *>(prm.tabB[1]), *gd2 = static_cast<const float *>(prm.tabD[1]);
   const float *gb3 = static_cast<const float *>(prm.tabB[2]), *gd3 = static_cast<const float *>(prm.tabD[2]);
   const float *u = static_cast<const float *>(prm.u);
-  float b1[A1], d1[A1], b2[A2], d2[A2], b3[A3], d3[A3], uv[AU];
+  float b1[A1], d1[A1], b2[A2], d2[A2], b3[A3 > 0 ? A3 : 1], d3[A3 > 0 ? A3 : 1], uv[AU];
 #pragma unroll
   for (int k = 0; k < A1; ++k) {
     const int i = tid + k * NT;

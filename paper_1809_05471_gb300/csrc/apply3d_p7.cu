@@ -7,11 +7,13 @@
 //   TMA ring, tile 2, 2, 4, tables reloaded for the transposed sweep
 //   register prefetch, tile 4, 2, 2
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
+// Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): tile 2, 2, 8, 7 warps; tile 2, 2, 6, 7 warps.
 // Factors evaluated on the fly (FP32): tile 2, 2, 2 first, then 2, 2, 1.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
 #include "apply3d_f32g.cuh"
 #include "apply3d_f32r.cuh"
+#include "apply3d_tc.cuh"
 
 namespace igasf {
 
@@ -19,6 +21,12 @@ int apply3d_p7(int prec, ApplyKernel *out, int max_out) {
   int n = 0;
   if (prec == IGASF_FP64) {
     if (n < max_out) out[n++] = make_apply3d<double, 7, 2, 2, 2>();
+    return n;
+  }
+  if (tensor_core_prec(prec)) {
+    const bool b = prec == IGASF_BF16_MMA;
+    if (n < max_out) out[n++] = b ? make_apply3d_tc<7, 2, 2, 8, TC_BF16, 7, 2>() : make_apply3d_tc<7, 2, 2, 8, TC_TF32, 7, 2>();
+    if (n < max_out) out[n++] = b ? make_apply3d_tc<7, 2, 2, 6, TC_BF16, 7, 2>() : make_apply3d_tc<7, 2, 2, 6, TC_TF32, 7, 2>();
     return n;
   }
   const bool bf = prec == IGASF_BF16;

@@ -7,11 +7,13 @@
 //   register prefetch, tile 2, 2, 2
 //   TMA ring, tile 4, 2, 1
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
+// Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): tile 2, 2, 8, 8 warps; tile 2, 2, 6, 8 warps.
 // Factors evaluated on the fly (FP32): tile 2, 2, 4 first, then 2, 2, 2.
 #include "apply3d.cuh"
 #include "apply3d_f32.cuh"
 #include "apply3d_f32g.cuh"
 #include "apply3d_f32r.cuh"
+#include "apply3d_tc.cuh"
 
 namespace igasf {
 
@@ -19,6 +21,12 @@ int apply3d_p8(int prec, ApplyKernel *out, int max_out) {
   int n = 0;
   if (prec == IGASF_FP64) {
     if (n < max_out) out[n++] = make_apply3d<double, 8, 2, 2, 2>();
+    return n;
+  }
+  if (tensor_core_prec(prec)) {
+    const bool b = prec == IGASF_BF16_MMA;
+    if (n < max_out) out[n++] = b ? make_apply3d_tc<8, 2, 2, 8, TC_BF16, 8, 2>() : make_apply3d_tc<8, 2, 2, 8, TC_TF32, 8, 2>();
+    if (n < max_out) out[n++] = b ? make_apply3d_tc<8, 2, 2, 6, TC_BF16, 8, 2>() : make_apply3d_tc<8, 2, 2, 6, TC_TF32, 8, 2>();
     return n;
   }
   const bool bf = prec == IGASF_BF16;

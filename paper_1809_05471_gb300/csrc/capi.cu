@@ -242,7 +242,8 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
   if (opt) o = *opt;
   for (int r : o.reserved)
     if (r != 0) return fail(IGASF_ERR_INVALID_ARG, "options.reserved must be zero");
-  if (o.kernel_variant < 0 || o.kernel_variant > IGASF_KERNEL_RING)
+  if (o.kernel_variant < 0 || o.kernel_variant == IGASF_KERNEL_ON_THE_FLY ||
+      o.kernel_variant > IGASF_KERNEL_MMA)
     return fail(IGASF_ERR_INVALID_ARG, "options.kernel_variant = %d", o.kernel_variant);
   if (o.default_prec < 0 || o.default_prec >= kNumPrec)
     return fail(IGASF_ERR_INVALID_ARG, "options.default_prec = %d", o.default_prec);

@@ -46,6 +46,18 @@ geo = {  # factors on the fly: (tile, Z of all slabs up front)
  8: [("2, 2, 4", 0), ("2, 2, 2", 0)],
  9: [("2, 2, 4", 0), ("2, 2, 2", 0)],
 }
+# tensor-core kernels of IGASF_TF32 / IGASF_BF16_MMA: (tile, warps per block,
+# minimum resident blocks asked of the register allocator), default first
+tc = {
+ 2: [("8, 8, 4", 8, 2), ("8, 8, 2", 8, 2)],
+ 3: [("8, 4, 4", 6, 2), ("4, 4, 4", 9, 2)],
+ 4: [("4, 4, 4", 8, 2), ("4, 4, 8", 8, 2)],
+ 5: [("4, 4, 4", 5, 2), ("2, 2, 8", 7, 2)],
+ 6: [("2, 2, 8", 9, 2), ("4, 2, 4", 6, 2)],
+ 7: [("2, 2, 8", 7, 2), ("2, 2, 6", 7, 2)],
+ 8: [("2, 2, 8", 8, 2), ("2, 2, 6", 8, 2)],
+ 9: [("2, 2, 8", 7, 2), ("2, 2, 6", 7, 2)],
+}
 mk = {R: "make_apply3d_f32r", T: "make_apply3d_f32"}
 name = {R: "register prefetch", T: "TMA ring"}
 for P in range(2, 10):
@@ -64,11 +76,18 @@ for P in range(2, 10):
         else:
             L.append("//   %s" % describe(c))
     L.append("// IGASF_TILE_SEARCH compiles every listed shape in both variants.")
+    L.append("// Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): %s." % "; ".join(
+        "tile %s, %d warps" % (t, w) for t, w, _ in tc[P]))
     L.append("// Factors evaluated on the fly (FP32): tile %s first, then %s." % (geo[P][0][0], geo[P][1][0]))
-    L.append('#include "apply3d.cuh"\n#include "apply3d_f32.cuh"\n#include "apply3d_f32g.cuh"\n#include "apply3d_f32r.cuh"\n\nnamespace igasf {\n')
+    L.append('#include "apply3d.cuh"\n#include "apply3d_f32.cuh"\n#include "apply3d_f32g.cuh"\n#include "apply3d_f32r.cuh"\n#include "apply3d_tc.cuh"\n\nnamespace igasf {\n')
     L.append("int apply3d_p%d(int prec, ApplyKernel *out, int max_out) {" % P)
     L.append("  int n = 0;\n  if (prec == IGASF_FP64) {")
     L.append("    if (n < max_out) out[n++] = make_apply3d<double, %d, %s>();\n    return n;\n  }" % (P, f64[P]))
+    L.append("  if (tensor_core_prec(prec)) {\n    const bool b = prec == IGASF_BF16_MMA;")
+    for t, w, mb in tc[P]:
+        L.append("    if (n < max_out) out[n++] = b ? make_apply3d_tc<%d, %s, TC_BF16, %d, %d>() : make_apply3d_tc<%d, %s, TC_TF32, %d, %d>();"
+                 % (P, t, w, mb, P, t, w, mb))
+    L.append("    return n;\n  }")
     L.append("  const bool bf = prec == IGASF_BF16;")
     L.append("#ifndef IGASF_TILE_SEARCH")
     def inst(c):

@@ -12,7 +12,7 @@
 namespace igasf {
 
 constexpr int kMaxDim = 3;
-constexpr int kNumPrec = 3;        // FP64, FP32, BF16
+constexpr int kNumPrec = 5;        // FP64, FP32, BF16, TF32, BF16_MMA
 constexpr int kFieldsK3 = 6;       // 11 12 13 22 23 33
 constexpr int kFieldsK2 = 3;       // 11 12 22
 
@@ -22,7 +22,11 @@ inline int num_fields(int d, int op) { return op == IGASF_MASS ? 1 : (d == 3 ? k
 // stored as double, float or bfloat16.
 inline bool vectors_are_float(int prec) { return prec != IGASF_FP64; }
 inline size_t vector_bytes(int prec) { return prec == IGASF_FP64 ? 8 : 4; }
-inline int factor_bytes(int prec) { return prec == IGASF_FP64 ? 8 : (prec == IGASF_FP32 ? 4 : 2); }
+inline int factor_bytes(int prec) {
+  return prec == IGASF_FP64 ? 8 : ((prec == IGASF_FP32 || prec == IGASF_TF32) ? 4 : 2);
+}
+// Precisions whose direction-3 contractions run on the tensor cores (3D only).
+inline bool tensor_core_prec(int prec) { return prec == IGASF_TF32 || prec == IGASF_BF16_MMA; }
 
 #ifdef __CUDACC__
 // Programmatic dependent launch: a tile kernel lets the gather that follows it

@@ -24,7 +24,7 @@ int apply2d_list(int p, int prec, ApplyKernel *out, int max_out);
 int list_apply_kernels(int d, int p, int prec, ApplyKernel *out, int max_out) {
   if (prec < 0 || prec >= kNumPrec) return 0;
   if (p < 2 || p > IGASF_MAX_ORDER || max_out < 1) return 0;
-  if (d == 2) return apply2d_list(p, prec, out, max_out);
+  if (d == 2) return tensor_core_prec(prec) ? 0 : apply2d_list(p, prec, out, max_out);
   if (d != 3) return 0;
   switch (p) {
     case 2: return apply3d_p2(prec, out, max_out);

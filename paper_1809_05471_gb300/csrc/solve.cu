@@ -310,7 +310,7 @@ extern "C" int igasf_cg_solve(igasf_handle h, int inner_prec, const double *b, d
   if (!h || !b || !x) return set_error(IGASF_ERR_INVALID_ARG, "handle, b and x must be non-NULL");
   if (h->d != 3) return set_error(IGASF_ERR_UNSUPPORTED, "the solver handles d = 3 plans");
   if (inner_prec < 0 || inner_prec >= kNumPrec)
-    return set_error(IGASF_ERR_INVALID_ARG, "inner_prec must be IGASF_FP64, IGASF_FP32 or IGASF_BF16");
+    return set_error(IGASF_ERR_INVALID_ARG, "inner_prec must be one of the igasf_prec values");
   if (!h->var[IGASF_FP64].present || !h->var[inner_prec].present)
     return set_error(IGASF_ERR_UNSUPPORTED, "the solve needs FP64 (and the inner precision) stored");
   if (!(rtol > 0.0) || !(inner_rtol > 0.0 && inner_rtol < 1.0) || max_iterations < 1)

@@ -23,6 +23,8 @@ STIFFNESS = 1
 FP64 = 0
 FP32 = 1
 BF16 = 2        # bfloat16-stored factors, float32 vectors and arithmetic
+TF32 = 3        # FP32 factors; direction-3 contractions on tensor cores, TF32 operands
+BF16_MMA = 4    # bfloat16-stored factors; direction-3 contractions on tensor cores, bf16 operands
 COEF_CONSTANT = 0
 COEF_EXP_SIN_COS = 1
 COEF_VALUES = 2
@@ -30,6 +32,7 @@ KERNEL_DEFAULT = 0
 KERNEL_REGISTERS = 1
 KERNEL_RING = 2
 KERNEL_ON_THE_FLY = 3
+KERNEL_MMA = 4
 GEOMETRY_STORED = 0
 GEOMETRY_ON_THE_FLY = 1     # FP32 applies evaluate the factors inside the tile kernel
 
@@ -207,7 +210,7 @@ class Plan:
         return self.handle
 
     def apply(self, op: int, u, v, prec: int = FP64, stream=None):
-        """v = A u on device tensors (float64 for FP64, float32 for FP32 and BF16)."""
+        """v = A u on device tensors (float64 for FP64, float32 for the others)."""
         _check(load_library().igasf_apply_prec(self._h(), int(op), int(prec), u.data_ptr(),
                                                v.data_ptr(), _stream_handle(stream)))
         return v

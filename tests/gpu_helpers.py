@@ -9,7 +9,11 @@ from paper_1809_05471_gb300 import igasf as G
 from paper_1809_05471_gb300 import inputs as I
 
 TOL = {G.FP64: 1e-12, G.FP32: 1e-5}
-DTYPE = {G.FP64: "float64", G.FP32: "float32", G.BF16: "float32"}
+DTYPE = {G.FP64: "float64", G.FP32: "float32", G.BF16: "float32", G.TF32: "float32",
+         G.BF16_MMA: "float32"}
+# unit roundoff of the tensor-core operand formats (round to nearest): TF32
+# keeps 11 significant bits, bfloat16 8
+UNIT_ROUNDOFF = {G.TF32: 2.0 ** -11, G.BF16_MMA: 2.0 ** -8}
 
 
 def tol(prec, patch_or_p):
@@ -22,11 +26,21 @@ def tol(prec, patch_or_p):
     has about 6p + 9 terms (three forward sweeps of p terms, the 3-term product
     with the factors, three transposed sweeps), so first-order rounding gives
     (6p + 9) 2^-24 relative to the absolute terms; the bar is twice that
-    (2.5e-6 at p = 2, 7.5e-6 at p = 9)."""
+    (2.5e-6 at p = 2, 7.5e-6 at p = 9).
+    TF32 and BF16_MMA (tensor-core direction-3 sweeps; BF16_MMA against the
+    oracle's operator with bfloat16-rounded factors): every product of the two
+    direction-3 contractions has both operands rounded once to the operand
+    format, a relative perturbation of at most 2u each, so to first order the
+    error is at most 4u times the absolute-value operator applied to |u|; the
+    bar takes that bound with the absolute operator's row sums at ||A||_inf,
+    i.e. 4u (TF32 2.0e-3, BF16 1.6e-2), plus the FP32 bar for the rest."""
     p = patch_or_p if isinstance(patch_or_p, (int, np.integer)) else int(patch_or_p.orders[0])
     if prec == G.FP64:
         return TOL[G.FP64]
-    return 2.0 * (6 * p + 9) * 2.0 ** -24
+    fp32 = 2.0 * (6 * p + 9) * 2.0 ** -24
+    if prec in UNIT_ROUNDOFF:
+        return 4.0 * UNIT_ROUNDOFF[prec] + fp32
+    return fp32
 
 
 def gpu_apply(plan, op, u, prec):

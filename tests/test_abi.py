@@ -157,7 +157,11 @@ def test_rejects_bad_geometry_options(lib):
     p2, _ = I.make_patch(2, 3, 4, seed=0)
     rc, _ = _setup(lib, 2, [3] * 2, p2.knots, p2.ctrl, opt=opt)
     assert rc == -4
-    for kv in (G.KERNEL_ON_THE_FLY, 4, -1):     # not selectable as kernel variants
+    opt = G.Options()
+    opt.kernel_variant = G.KERNEL_MMA               # valid, but FP64 has no tensor-core kernel
+    rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, opt=opt)
+    assert rc == -4
+    for kv in (G.KERNEL_ON_THE_FLY, 5, -1):     # not selectable as kernel variants
         opt = G.Options()
         opt.kernel_variant = kv
         rc, _ = _setup(lib, 3, [3] * 3, pt.knots, pt.ctrl, opt=opt)
@@ -222,6 +226,11 @@ def test_list_kernels_enumerates_selectable_candidates(lib):
                     assert v in (G.KERNEL_REGISTERS, G.KERNEL_RING)
                 if prec == G.FP64:
                     assert all(v == G.KERNEL_REGISTERS for _, v in cands)
+            for prec in (G.TF32, G.BF16_MMA):       # tensor-core kernels: 3D only
+                cands = G.list_kernels(d, p, prec)
+                assert (len(cands) >= 1) == (d == 3)
+                assert all(v == G.KERNEL_MMA for _, v in cands)
+                assert len({tuple(t) for t, _ in cands}) == len(cands)
             geo = G.list_kernels(d, p, G.FP32, G.GEOMETRY_ON_THE_FLY)
             assert (len(geo) >= 1) == (d == 3)
             assert all(v == G.KERNEL_ON_THE_FLY for _, v in geo)

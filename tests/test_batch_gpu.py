@@ -22,7 +22,7 @@ def _small_batch(n, seed):
     return out
 
 
-@pytest.mark.parametrize("prec", [G.FP32, G.FP64, G.BF16])
+@pytest.mark.parametrize("prec", [G.FP32, G.FP64, G.BF16, G.TF32, G.BF16_MMA])
 def test_batch_equals_individual_applies(prec):
     import torch
     dt = torch.float64 if prec == G.FP64 else torch.float32
@@ -30,7 +30,7 @@ def test_batch_equals_individual_applies(prec):
     # force two kernel variants on patches of the same order to get several groups
     plans = []
     for i, (pt, _) in enumerate(patches):
-        kv = G.KERNEL_RING if (prec != G.FP64 and i % 2) else 0
+        kv = G.KERNEL_RING if (prec in (G.FP32, G.BF16) and i % 2) else 0
         plans.append(G.Plan.from_patch(pt, precisions=(prec,), kernel_variant=kv))
     u = np.concatenate([u for _, u in patches])
     ud = torch.as_tensor(u, device="cuda").to(dt)
@@ -53,7 +53,7 @@ def test_batch_equals_individual_applies(prec):
         for k in (0, 5):
             pt, uk = patches[k]
             rows = sample_rows(pt, 16, seed=k)
-            with O.stored_factor_bits(O.BF16_BITS if prec == G.BF16 else 0):
+            with O.stored_factor_bits(O.BF16_BITS if prec in (G.BF16, G.BF16_MMA) else 0):
                 vr, ra = O.apply_rows(pt, O.STIFFNESS, uk, rows)
             a = batch.offsets[k]
             vk = v[a:a + pt.num_dofs].double().cpu().numpy()[rows]
