@@ -1,6 +1,7 @@
 // FP32 tile kernel, register-prefetch variant: the same packed FP32x2 sweeps as
 // apply3d_f32.cuh, but each thread loads its own factors straight from HBM into
-// registers, PD slabs ahead (the first PD slabs at kernel entry). No producer
+// registers, PD slabs ahead (the first PD slabs at kernel entry; PD scaled up
+// for slabs narrower than FP32 stiffness ones). No producer
 // warp and no shared-memory ring: fewer instructions and no barrier waits,
 // fewer bytes in flight. Which variant is faster depends on the order and the
 // tile (both are tile-search candidates).
@@ -95,6 +96,12 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
   constexpr int H1 = G::H1, PP = G::PP, NT = G::NT, NPAIR = G::NPAIR, UNITS = G::UNITS;
   constexpr int NCH = STIFF ? 3 : 1;   // chunks of a pencil pair per slab
   using Chunk = typename FactorChunk<STIFF, BF>::type;
+  // Slabs in flight per thread. PD counts slabs of FP32 stiffness factors (48
+  // bytes per thread and slab); narrower slabs (bfloat16, or the mass's single
+  // field) are requested proportionally further ahead, so that every variant
+  // keeps about the same bytes in flight (at most the tile's Q3 slabs).
+  constexpr int SLABB = NCH * (int)sizeof(Chunk);
+  constexpr int PDX = cmin(Q3, cmax(PD, PD * 48 / SLABB));
 
   extern __shared__ __align__(16) unsigned char smem_f32r[];
   float *sm = reinterpret_cast<float *>(smem_f32r);
@@ -115,12 +122,12 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
   const int ke3 = min(S3, prm.K[2] - e03);
   const int nslab = ke3 * P;
 
-  // ---- request the first PD slabs of factors now (consumed in phase C)
+  // ---- request the first PDX slabs of factors now (consumed in phase C)
   const bool has_pair = tid < NPAIR;
-  Chunk dq[PD][NCH];
+  Chunk dq[PDX][NCH];
   const Chunk *Dc = reinterpret_cast<const Chunk *>(prm.D) + (size_t)tile * Q3 * NCH * UNITS + tid;
 #pragma unroll
-  for (int s = 0; s < PD; ++s) {
+  for (int s = 0; s < PDX; ++s) {
     if (has_pair && s < nslab) {
 #pragma unroll
       for (int c = 0; c < NCH; ++c) dq[s][c] = ldg_stream(Dc + ((size_t)s * NCH + c) * UNITS);
@@ -211,19 +218,19 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
 #pragma unroll
         for (int qq = 0; qq < P; ++qq) {
           const int q3 = e3 * P + qq;
-          // factors of this slab, then request slab q3 + PD into the freed slot
+          // factors of this slab, then request slab q3 + PDX into the freed slot
           float4 dc[NCH] = {};
           float2 dm = make_float2(0.f, 0.f);
           if constexpr (STIFF) {
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) dc[c] = widen(dq[q3 % PD][c]);
+            for (int c = 0; c < NCH; ++c) dc[c] = widen(dq[q3 % PDX][c]);
           } else {
-            dm = widen(dq[q3 % PD][0]);
+            dm = widen(dq[q3 % PDX][0]);
           }
-          if (q3 + PD < nslab) {
+          if (q3 + PDX < nslab) {
 #pragma unroll
             for (int c = 0; c < NCH; ++c)
-              dq[q3 % PD][c] = ldg_stream(Dc + ((size_t)(q3 + PD) * NCH + c) * UNITS);
+              dq[q3 % PDX][c] = ldg_stream(Dc + ((size_t)(q3 + PDX) * NCH + c) * UNITS);
           }
           float2 b[PP], db[PP];
           {

@@ -50,9 +50,6 @@ namespace igasf {
 
 enum { TC_TF32 = 0, TC_BF16 = 1 };
 
-__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
-__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
-
 __device__ __forceinline__ uint32_t tf32_bits(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -176,6 +173,28 @@ __device__ __forceinline__ void apply3d_tc_body(const ApplyParams &prm, const in
   const int e01 = t1 * S1, e02 = t2 * S2, e03 = t3 * S3;
   const int ke3 = min(S3, prm.K[2] - e03);
   const int nslab = ke3 * P;
+
+  // ---- factor chunks of m-tile mtl, n-tile nt: its pairs at slabs 8 nt + 2t + s,
+  // s = 0, 1 (zero beyond the patch or the layout row). The warp's first m-tile
+  // requests its first n-tile now, so that the latency overlaps the staging and
+  // phases A and B; later n-tiles are requested one step ahead, and the next
+  // m-tile's first n-tile during the last step of the current one.
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const Chunk *Dc = reinterpret_cast<const Chunk *>(prm.D) + (size_t)tile * Q3 * NCH * UNITS;
+  auto load_factors = [&](const int mtl, const int nt, Chunk (&fc)[2][NCH]) {
+    const int un = 8 * mtl + g;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int q3 = 8 * nt + 2 * t + s;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        if (un < UNITS && q3 < nslab) fc[s][c] = ldg_stream(Dc + ((size_t)q3 * NCH + c) * UNITS + un);
+        else fc[s][c] = Chunk{};
+      }
+    }
+  };
+  Chunk fc[2][2][NCH];
+  if (warp < NMT) load_factors(warp, 0, fc[0]);
 
   // ---- stage: direction-1/2 tables and the u box (as the packed kernels) ...
   stage_tile_f32<P, S1, S2, S3, NT, STIFF, false>(prm, tid, e01, e02, e03, t1b, t1d, t2b, t2d,
@@ -307,14 +326,24 @@ __device__ __forceinline__ void apply3d_tc_body(const ApplyParams &prm, const in
   // thread's pair at its two slabs, and the transposed products into the dof
   // accumulators W3 = B3'^T g3, W2 = B3^T g2, W1 = B3^T g1 (mass: u, w = D u, B3^T w).
   {
-    const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const Chunk *Dc = reinterpret_cast<const Chunk *>(prm.D) + (size_t)tile * Q3 * NCH * UNITS;
+    const bool full = nslab == Q3;   // no ragged slabs: the next m-tile's loads may start early
     const float2 *Yf[3] = {Y0, STIFF ? Y1 : Y0, STIFF ? Y2 : Y0};
     const uint2 *fw2 = reinterpret_cast<const uint2 *>(fw);
     const uint2 *bw2 = reinterpret_cast<const uint2 *>(bw);
     for (int mt = warp; mt < NMT; mt += NW) {
       const int unit = 8 * mt + g;
-      const bool uok = unit < UNITS;
+      const bool more = mt + NW < NMT;
+      if (mt != warp) {
+        if (!full) {
+          load_factors(mt, 0, fc[0]);
+        } else if constexpr (MK == TC_TF32 && (NQT & 1)) {
+          // requested into the buffer after the last n-tile's
+#pragma unroll
+          for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) fc[0][s2][c] = fc[1][s2][c];
+        }
+      }
       float za[NF][JT][4];
 #pragma unroll
       for (int f = 0; f < NF; ++f)
@@ -322,18 +351,6 @@ __device__ __forceinline__ void apply3d_tc_body(const ApplyParams &prm, const in
         for (int jt = 0; jt < JT; ++jt)
 #pragma unroll
           for (int c = 0; c < 4; ++c) za[f][jt][c] = 0.f;
-      // factor chunks of n-tile nt: slabs 8 nt + 2t + s, s = 0, 1
-      auto load_factors = [&](int nt, Chunk (&fc)[2][NCH]) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const int q3 = 8 * nt + 2 * t + s;
-#pragma unroll
-          for (int c = 0; c < NCH; ++c) {
-            if (uok && q3 < nslab) fc[s][c] = ldg_stream(Dc + ((size_t)q3 * NCH + c) * UNITS + unit);
-            else fc[s][c] = Chunk{};
-          }
-        }
-      };
       // forward product of n-tile nt and product with the factors: gq[f][4]
       // holds g (stiffness: g1, g2, g3; mass: w) at the accumulator positions
       auto forward_product = [&](const int nt, const Chunk (&fc)[2][NCH], float (&gq)[NF][4]) {
@@ -419,14 +436,13 @@ __device__ __forceinline__ void apply3d_tc_body(const ApplyParams &prm, const in
         }
       };
 
-      Chunk fc[2][2][NCH];
-      load_factors(0, fc[0]);
 #pragma unroll
       for (int s = 0; s < NSTEP; ++s) {
         if constexpr (MK == TC_TF32) {
           const int nt = s;
           if (8 * nt < nslab) {
-            if (nt + 1 < NQT) load_factors(nt + 1, fc[(nt + 1) & 1]);
+            if (nt + 1 < NQT) load_factors(mt, nt + 1, fc[(nt + 1) & 1]);
+            else if (full && more) load_factors(mt + NW, 0, fc[(nt + 1) & 1]);
             float gq[NF][4];
             forward_product(nt, fc[nt & 1], gq);
             transposed(s, gq, gq);
@@ -439,12 +455,13 @@ __device__ __forceinline__ void apply3d_tc_body(const ApplyParams &prm, const in
             for (int f = 0; f < NF; ++f)
 #pragma unroll
               for (int c = 0; c < 4; ++c) gqb[f][c] = 0.f;
-            if (nb < NQT) load_factors(nb, fc[1]);
+            if (nb < NQT) load_factors(mt, nb, fc[1]);
             forward_product(na, fc[0], gqa);
-            if (nb < NQT && 8 * nb < nslab) {
-              if (nb + 1 < NQT) load_factors(nb + 1, fc[0]);
-              forward_product(nb, fc[1], gqb);
-            }
+            // the next request into the freed buffer: n-tile nb + 1 of this
+            // m-tile, or the next m-tile's first n-tile
+            if (nb + 1 < NQT) load_factors(mt, nb + 1, fc[0]);
+            else if (full && more) load_factors(mt + NW, 0, fc[0]);
+            if (nb < NQT && 8 * nb < nslab) forward_product(nb, fc[1], gqb);
             transposed(s, gqa, gqb);
           }
         }
