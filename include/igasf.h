@@ -365,10 +365,32 @@ int igasf_cg_solve(igasf_handle h, int inner_prec, const double *b, double *x, d
  * The first apply with a given (u, v), and every change of them, uploads the
  * per-patch pointer tables (a short synchronous copy). Results equal the
  * patches' individual applies bit for bit. Errors: INVALID_ARG, UNSUPPORTED
- * (a plan lacks `prec`, or is 2D), CUDA, OOM.
+ * (a plan lacks `prec`, or is 2D), CUDA, OOM. igasf_batch_info reports 1 launch
+ * group for the persistent schedule.
  */
 typedef struct igasf_batch_s *igasf_batch;
 int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, igasf_batch *out);
+
+/*
+ * As igasf_batch_create with a choice of schedule:
+ *   IGASF_BATCH_GRAPH: the graph of one launch per tile kernel described above
+ *     (what igasf_batch_create builds);
+ *   IGASF_BATCH_PERSISTENT: one persistent launch (as many blocks as fit on the
+ *     GPU) whose blocks walk a work list of every patch's tiles, highest order
+ *     first, then the gather, captured as one graph. It runs FP32 or BF16 3D
+ *     plans of order 2..6 set up with the persistent tile shape of their order
+ *     (igasf_batch_persistent_tile; pass it as options.tile), other plans give
+ *     IGASF_ERR_UNSUPPORTED. Each tile runs the register-prefetch kernel's
+ *     arithmetic: results equal the individual applies of plans set up with
+ *     that variant (options.kernel_variant = IGASF_KERNEL_REGISTERS) bit for
+ *     bit.
+ */
+enum { IGASF_BATCH_GRAPH = 0, IGASF_BATCH_PERSISTENT = 1 };
+int igasf_batch_create_ex(int nplans, const igasf_handle *plans, int op, int prec, int schedule,
+                          igasf_batch *out);
+/* The tile shape (3 ints) the persistent schedule runs for order p in precision
+ * prec; IGASF_ERR_UNSUPPORTED if it runs none. Host-only. */
+int igasf_batch_persistent_tile(int p, int prec, int *tile);
 int igasf_batch_apply(igasf_batch b, const void *u, void *v, void *stream);
 int igasf_batch_info(igasf_batch b, int64_t *total_dofs, int64_t *total_quad_points,
                      int64_t *factor_bytes, int *launch_groups);

@@ -88,12 +88,17 @@ struct TileF2R {
   }
 };
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL>
+// NTX: block size when it is not the tile's own (0); a persistent kernel that
+// runs tiles of several orders in blocks of one size passes its block size,
+// which must cover the tile's pencil pairs.
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL, int NTX = 0>
 __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const int tile) {
   using G = TileF2R<P, S1, S2, S3>;
   constexpr int E1 = G::E1, E2 = G::E2, E3 = G::E3;
   constexpr int Q1 = G::Q1, Q2 = G::Q2, Q3 = G::Q3;
-  constexpr int H1 = G::H1, PP = G::PP, NT = G::NT, NPAIR = G::NPAIR, UNITS = G::UNITS;
+  constexpr int H1 = G::H1, PP = G::PP, NPAIR = G::NPAIR, UNITS = G::UNITS;
+  constexpr int NT = NTX ? NTX : G::NT;
+  static_assert(NT >= NPAIR, "the block must cover the tile's pencil pairs");
   constexpr int NCH = STIFF ? 3 : 1;   // chunks of a pencil pair per slab
   using Chunk = typename FactorChunk<STIFF, BF>::type;
   // Slabs in flight per thread. PD counts slabs of FP32 stiffness factors (48

@@ -103,6 +103,13 @@ struct igasf_batch_s {
   igasf::GatherParams *d_gp = nullptr;
   int *d_gblock_patch = nullptr, *d_gfirst = nullptr;
   int gblocks = 0;
+  // schedule IGASF_BATCH_PERSISTENT: one launch over a (patch, tile) work list
+  bool persistent = false;
+  std::vector<igasf::ApplyParams> p_params;  // per patch
+  igasf::ApplyParams *d_pparams = nullptr;
+  int *d_porder = nullptr;
+  int2 *d_items = nullptr;
+  int nitems = 0, pgrid = 0;
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -119,6 +126,9 @@ void free_batch(igasf_batch b) {
     cudaFree(g.d_block_patch);
     cudaFree(g.d_first_block);
   }
+  cudaFree(b->d_pparams);
+  cudaFree(b->d_porder);
+  cudaFree(b->d_items);
   cudaFree(b->d_gp);
   cudaFree(b->d_gblock_patch);
   cudaFree(b->d_gfirst);
@@ -147,6 +157,12 @@ cudaError_t bind_vectors(igasf_batch b, const void *u, void *v) {
       e = cudaMemcpy(g.d_params, g.h_params.data(), sizeof(igasf::ApplyParams) * g.h_params.size(),
                      cudaMemcpyHostToDevice);
   }
+  if (b->persistent) {
+    for (int i = 0; i < b->n; ++i) b->p_params[i].u = static_cast<const char *>(u) + es * b->offset[i];
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->d_pparams, b->p_params.data(), sizeof(igasf::ApplyParams) * b->n,
+                     cudaMemcpyHostToDevice);
+  }
   for (int i = 0; i < b->n; ++i) b->h_gp[i].v = static_cast<char *>(v) + es * b->offset[i];
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_gp, b->h_gp.data(), sizeof(igasf::GatherParams) * b->h_gp.size(),
@@ -161,19 +177,37 @@ cudaError_t bind_vectors(igasf_batch b, const void *u, void *v) {
 extern "C" {
 
 int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, igasf_batch *out) {
+  return igasf_batch_create_ex(nplans, plans, op, prec, IGASF_BATCH_GRAPH, out);
+}
+
+int igasf_batch_create_ex(int nplans, const igasf_handle *plans, int op, int prec, int schedule,
+                          igasf_batch *out) {
   using namespace igasf;
   if (!out || !plans || nplans < 1) return set_error(IGASF_ERR_INVALID_ARG, "need nplans >= 1, plans and out");
   if (op != IGASF_MASS && op != IGASF_STIFFNESS) return set_error(IGASF_ERR_INVALID_ARG, "bad op");
   if (prec < 0 || prec >= kNumPrec) return set_error(IGASF_ERR_INVALID_ARG, "bad prec");
+  if (schedule != IGASF_BATCH_GRAPH && schedule != IGASF_BATCH_PERSISTENT)
+    return set_error(IGASF_ERR_INVALID_ARG, "bad schedule");
+  const bool pers = schedule == IGASF_BATCH_PERSISTENT;
   for (int i = 0; i < nplans; ++i) {
     const igasf_plan *h = plans[i];
     if (!h) return set_error(IGASF_ERR_INVALID_ARG, "a plan is NULL");
     if (!h->var[prec].present) return set_error(IGASF_ERR_UNSUPPORTED, "a plan lacks the batch precision");
     if (!h->var[prec].k.launch_batched[op])
       return set_error(IGASF_ERR_UNSUPPORTED, "a plan's kernel has no batched form (2D plans)");
+    if (pers) {
+      int S[3];
+      const ApplyKernel &k = h->var[prec].k;
+      if (h->d != 3 || h->var[prec].on_the_fly || !persistent_tile(h->p, prec, S) || k.S[0] != S[0] ||
+          k.S[1] != S[1] || k.S[2] != S[2])
+        return set_error(IGASF_ERR_UNSUPPORTED,
+                         "the persistent schedule needs FP32 or BF16 3D plans of order 2..6 set up with "
+                         "the persistent tile of their order (igasf_batch_persistent_tile)");
+    }
   }
   igasf_batch b = new (std::nothrow) igasf_batch_s();
   if (!b) return set_error(IGASF_ERR_OOM, "host allocation");
+  b->persistent = pers;
   b->n = nplans;
   b->op = op;
   b->prec = prec;
@@ -203,6 +237,7 @@ int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, 
     make_apply_params(h, v, op, nullptr, v.vpart, &prm);
     prm.skip_slab = -1;
     G.h_params.push_back(prm);
+    if (pers) b->p_params.push_back(prm);
     GatherParams &gp = b->h_gp[i];
     gp.vpart = v.vpart;
     gp.N0 = h->N[0];
@@ -248,17 +283,38 @@ int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, 
     if (e == cudaSuccess) e = upload(&b->d_gfirst, first);
     if (e == cudaSuccess) e = upload(&b->d_gp, b->h_gp);
   }
+  // the persistent schedule's work list: (patch, tile), highest order first
+  if (e == cudaSuccess && pers) {
+    std::vector<int> order(b->n);
+    std::vector<int2> items;
+    for (int i = 0; i < b->n; ++i) order[i] = b->plans[i]->p;
+    for (int p = 9; p >= 1; --p)
+      for (int i = 0; i < b->n; ++i)
+        if (order[i] == p)
+          for (int t = 0; t < b->p_params[i].ntiles; ++t) items.push_back(make_int2(i, t));
+    b->nitems = (int)items.size();
+    e = prepare_persistent(op, prec, &b->pgrid);
+    if (e == cudaSuccess) e = upload(&b->d_pparams, b->p_params);
+    if (e == cudaSuccess) e = upload(&b->d_porder, order);
+    if (e == cudaSuccess) e = upload(&b->d_items, items);
+  }
   // capture the launches into a graph
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    for (auto &G : b->groups) {
-      BatchParams bp;
-      bp.params = G.d_params;
-      bp.block_patch = G.d_block_patch;
-      bp.first_block = G.d_first_block;
-      const cudaError_t le = G.k.launch_batched[op](bp, G.blocks, b->cap);
+    if (pers) {
+      const cudaError_t le = launch_persistent(op, prec, b->d_pparams, b->d_porder, b->d_items,
+                                               b->nitems, b->pgrid, b->cap);
       if (le != cudaSuccess && e == cudaSuccess) e = le;
+    } else {
+      for (auto &G : b->groups) {
+        BatchParams bp;
+        bp.params = G.d_params;
+        bp.block_patch = G.d_block_patch;
+        bp.first_block = G.d_first_block;
+        const cudaError_t le = G.k.launch_batched[op](bp, G.blocks, b->cap);
+        if (le != cudaSuccess && e == cudaSuccess) e = le;
+      }
     }
     if (vectors_are_float(prec))
       batched_gather_kernel<float><<<b->gblocks, kGatherThreads, 0, b->cap>>>(b->d_gp, b->d_gblock_patch,
@@ -303,7 +359,14 @@ int igasf_batch_info(igasf_batch b, int64_t *total_dofs, int64_t *total_quad_poi
   if (total_dofs) *total_dofs = b->total_dofs;
   if (total_quad_points) *total_quad_points = b->total_qp;
   if (factor_bytes) *factor_bytes = b->factor_bytes;
-  if (launch_groups) *launch_groups = (int)b->groups.size();
+  if (launch_groups) *launch_groups = b->persistent ? 1 : (int)b->groups.size();
+  return IGASF_OK;
+}
+
+int igasf_batch_persistent_tile(int p, int prec, int *tile) {
+  if (!tile) return igasf::set_error(IGASF_ERR_INVALID_ARG, "tile is NULL");
+  if (!igasf::persistent_tile(p, prec, tile))
+    return igasf::set_error(IGASF_ERR_UNSUPPORTED, "no persistent tile for this order and precision");
   return IGASF_OK;
 }
 

@@ -139,6 +139,13 @@ cudaError_t launch_export_factors(const FactorLayout &L, int op, int64_t Qtot, c
 cudaError_t launch_gather(int d, int float_vectors, const void *vpart, void *v, const int *N,
                           const int *T, const int *S, int p, int2 *const *gtab, cudaStream_t s);
 void gather_table(int N, int S, int E, int T, std::vector<int2> &out);
+// The persistent batch kernel (batch_persistent.cu): the tile shape it runs for
+// order p in precision prec (false if none), its grid on the current device,
+// and its launch over a work list of (patch, tile) items.
+bool persistent_tile(int p, int prec, int *S);
+cudaError_t prepare_persistent(int op, int prec, int *grid);
+cudaError_t launch_persistent(int op, int prec, const ApplyParams *params, const int *order,
+                              const int2 *items, int nitems, int grid, cudaStream_t s);
 // Locate the static scratch array of igasf_apply_noalloc on `device` (current)
 // and cache its address (noalloc.cu).
 void noalloc_prepare(int device);

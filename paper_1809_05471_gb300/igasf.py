@@ -33,6 +33,8 @@ KERNEL_REGISTERS = 1
 KERNEL_RING = 2
 KERNEL_ON_THE_FLY = 3
 KERNEL_MMA = 4
+BATCH_GRAPH = 0
+BATCH_PERSISTENT = 1        # one persistent launch over a (patch, tile) work list
 GEOMETRY_STORED = 0
 GEOMETRY_ON_THE_FLY = 1     # FP32 applies evaluate the factors inside the tile kernel
 
@@ -47,7 +49,7 @@ EXPORTED = [
     "igasf_num_dofs", "igasf_num_quad_points", "igasf_describe", "igasf_get_tables",
     "igasf_get_factors", "igasf_quad_points", "igasf_profile_begin", "igasf_profile_end", "igasf_apply_noalloc",
     "igasf_device_status", "igasf_set_test_fault", "igasf_cg_solve",
-    "igasf_batch_create", "igasf_batch_apply", "igasf_batch_info", "igasf_batch_destroy",
+    "igasf_batch_create", "igasf_batch_create_ex", "igasf_batch_persistent_tile", "igasf_batch_apply", "igasf_batch_info", "igasf_batch_destroy",
     "igasf_autotune", "igasf_list_kernels", "igasf_assembled_nnz", "igasf_assemble_csr",
     "igasf_last_error_message", "igasf_version",
 ]
@@ -118,6 +120,9 @@ def load_library(path: str = LIB_PATH):
                                    ctypes.c_int, ctypes.POINTER(CgReport), vp]
     lib.igasf_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(vp)]
+    lib.igasf_batch_create_ex.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.POINTER(vp)]
+    lib.igasf_batch_persistent_tile.argtypes = [ctypes.c_int, ctypes.c_int, ip]
     lib.igasf_batch_apply.argtypes = [vp, vp, vp, vp]
     i64p = ctypes.POINTER(ctypes.c_int64)
     lib.igasf_batch_info.argtypes = [vp, i64p, i64p, i64p, ip]
@@ -372,15 +377,24 @@ def autotune(patch, op: int = STIFFNESS, prec: int = FP32, repeats: int = 5):
     return list(tile), int(variant.value), float(ms.value)
 
 
+def batch_persistent_tile(p: int, prec: int = FP32):
+    """Tile shape the persistent batch schedule runs for order p (host-only)."""
+    t = (ctypes.c_int * 3)()
+    _check(load_library().igasf_batch_persistent_tile(int(p), int(prec), t))
+    return [int(x) for x in t]
+
+
 class Batch:
     """igasf_batch over plans (which must outlive it): one graph launch per apply."""
 
-    def __init__(self, plans: Sequence[Plan], op: int = STIFFNESS, prec: int = FP32):
+    def __init__(self, plans: Sequence[Plan], op: int = STIFFNESS, prec: int = FP32,
+                 schedule: int = BATCH_GRAPH):
         lib = load_library()
         self.plans = list(plans)
         arr = (ctypes.c_void_p * len(self.plans))(*[p._h().value for p in self.plans])
         h = ctypes.c_void_p()
-        _check(lib.igasf_batch_create(len(self.plans), arr, int(op), int(prec), ctypes.byref(h)))
+        _check(lib.igasf_batch_create_ex(len(self.plans), arr, int(op), int(prec), int(schedule),
+                                         ctypes.byref(h)))
         self.handle = h
         self.offsets = np.cumsum([0] + [p.num_dofs for p in self.plans])
         td, tq, fb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
