@@ -1,7 +1,7 @@
 // FP32 tile kernel, register-prefetch variant: the same packed FP32x2 sweeps as
 // apply3d_f32.cuh, but each thread loads its own factors straight from HBM into
 // registers, PD slabs ahead (the first PD slabs at kernel entry; PD scaled up
-// for slabs narrower than FP32 stiffness ones). No producer
+// for the narrow slabs of the mass). No producer
 // warp and no shared-memory ring: fewer instructions and no barrier waits,
 // fewer bytes in flight. Which variant is faster depends on the order and the
 // tile (both are tile-search candidates).
@@ -102,11 +102,13 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
   constexpr int NCH = STIFF ? 3 : 1;   // chunks of a pencil pair per slab
   using Chunk = typename FactorChunk<STIFF, BF>::type;
   // Slabs in flight per thread. PD counts slabs of FP32 stiffness factors (48
-  // bytes per thread and slab); narrower slabs (bfloat16, or the mass's single
-  // field) are requested proportionally further ahead, so that every variant
-  // keeps about the same bytes in flight (at most the tile's Q3 slabs).
+  // bytes per thread and slab); the mass's single-field slabs (8 or 4 bytes)
+  // are requested proportionally further ahead, so that they keep about the
+  // same bytes in flight (at most the tile's Q3 slabs). The bfloat16 stiffness
+  // keeps PD: twice as many slabs ahead raised its registers to 154 and cost a
+  // resident block per SM (64^3, p = 4: 61 -> 67 us).
   constexpr int SLABB = NCH * (int)sizeof(Chunk);
-  constexpr int PDX = cmin(Q3, cmax(PD, PD * 48 / SLABB));
+  constexpr int PDX = STIFF ? PD : cmin(Q3, cmax(PD, PD * 48 / SLABB));
 
   extern __shared__ __align__(16) unsigned char smem_f32r[];
   float *sm = reinterpret_cast<float *>(smem_f32r);
