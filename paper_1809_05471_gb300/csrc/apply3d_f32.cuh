@@ -212,6 +212,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   return true;
 }
 
+// Bulk prefetch of `bytes` contiguous bytes of global memory into L2 (the TMA
+// engine; no registers, no completion to wait for). Address and size
+// multiples of 16 bytes.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// The factor slabs 0..nslab-1 of one tile (slab_bytes each, contiguous from
+// base) requested into L2 by the block's first threads, one slab each.
+__device__ __forceinline__ void prefetch_tile_factors(const void *base, uint32_t slab_bytes, int nslab,
+                                                      int tid, int nthreads) {
+  for (int s = tid; s < nslab; s += nthreads)
+    prefetch_l2_bulk(static_cast<const unsigned char *>(base) + (size_t)s * slab_bytes, slab_bytes);
+}
+
 // Global -> shared bulk copy completing on an mbarrier (sizes and addresses
 // multiples of 16 bytes).
 __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes,

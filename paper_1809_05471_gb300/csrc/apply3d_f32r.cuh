@@ -129,10 +129,13 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
   const int ke3 = min(S3, prm.K[2] - e03);
   const int nslab = ke3 * P;
 
-  // ---- request the first PDX slabs of factors now (consumed in phase C)
+  // ---- the tile's factors into L2 now, so that the stream from DRAM runs
+  // during staging and phases A and B, and the register loads of phase C hit
+  // L2; then the first PDX slabs into registers (consumed in phase C)
   const bool has_pair = tid < NPAIR;
   Chunk dq[PDX][NCH];
   const Chunk *Dc = reinterpret_cast<const Chunk *>(prm.D) + (size_t)tile * Q3 * NCH * UNITS + tid;
+  prefetch_tile_factors(Dc - tid, (uint32_t)(NCH * UNITS * sizeof(Chunk)), nslab, tid, NT);
 #pragma unroll
   for (int s = 0; s < PDX; ++s) {
     if (has_pair && s < nslab) {

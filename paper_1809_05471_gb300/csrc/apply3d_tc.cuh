@@ -193,6 +193,9 @@ __device__ __forceinline__ void apply3d_tc_body(const ApplyParams &prm, const in
       }
     }
   };
+  // the tile's factors into L2 (the stream from DRAM then runs during staging
+  // and phases A and B; phase C's loads hit L2)
+  prefetch_tile_factors(Dc, (uint32_t)(NCH * UNITS * sizeof(Chunk)), nslab, tid, NT);
   Chunk fc[2][2][NCH];
   if (warp < NMT) load_factors(warp, 0, fc[0]);
 
