@@ -212,19 +212,37 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   return true;
 }
 
-// Bulk prefetch of `bytes` contiguous bytes of global memory into L2 (the TMA
-// engine; no registers, no completion to wait for). Address and size
-// multiples of 16 bytes.
-__device__ __forceinline__ void prefetch_l2_bulk(const void *src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+// L2 policy for data read once: its lines are the first to be evicted, so a
+// prefetched factor stream does not push out what the gather reads back.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
 }
 
-// The factor slabs 0..nslab-1 of one tile (slab_bytes each, contiguous from
-// base) requested into L2 by the block's first threads, one slab each.
-__device__ __forceinline__ void prefetch_tile_factors(const void *base, uint32_t slab_bytes, int nslab,
-                                                      int tid, int nthreads) {
-  for (int s = tid; s < nslab; s += nthreads)
-    prefetch_l2_bulk(static_cast<const unsigned char *>(base) + (size_t)s * slab_bytes, slab_bytes);
+// Bulk prefetch of `bytes` contiguous bytes of global memory into L2 (the TMA
+// engine; no registers, no completion to wait for), with an L2 policy.
+// Address and size multiples of 16 bytes.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *src, uint32_t bytes, uint64_t pol) {
+  asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(src), "r"(bytes),
+               "l"(pol)
+               : "memory");
+}
+
+// Factor slabs s0 .. s1 - 1 of one tile (slab_bytes each, contiguous from
+// base) requested into L2 as evict-first lines, one slab per thread.
+__device__ __forceinline__ void prefetch_factor_slabs(const void *base, uint32_t slab_bytes, int s0,
+                                                      int s1, int tid, int nthreads) {
+  if (s0 + tid >= s1) return;
+  const uint64_t pol = l2_evict_first_policy();
+  for (int s = s0 + tid; s < s1; s += nthreads)
+    prefetch_l2_bulk(static_cast<const unsigned char *>(base) + (size_t)s * slab_bytes, slab_bytes, pol);
+}
+
+// Slabs a tile kernel requests into L2 at entry: about 96 KB (at most the
+// tile's Q3 slabs), so that the resident blocks' requests stay within L2.
+__host__ __device__ constexpr int l2_window_slabs(int slab_bytes, int q3) {
+  return (98304 / slab_bytes) < 1 ? 1 : ((98304 / slab_bytes) > q3 ? q3 : (98304 / slab_bytes));
 }
 
 // Global -> shared bulk copy completing on an mbarrier (sizes and addresses

@@ -129,13 +129,15 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
   const int ke3 = min(S3, prm.K[2] - e03);
   const int nslab = ke3 * P;
 
-  // ---- the tile's factors into L2 now, so that the stream from DRAM runs
-  // during staging and phases A and B, and the register loads of phase C hit
-  // L2; then the first PDX slabs into registers (consumed in phase C)
+  // ---- the tile's factors (up to about 96 KB of them) into L2 now, as
+  // evict-first lines: the stream from DRAM runs during staging and phases A
+  // and B, and the register loads of phase C hit L2; then the first PDX slabs
+  // into registers (consumed in phase C)
   const bool has_pair = tid < NPAIR;
   Chunk dq[PDX][NCH];
   const Chunk *Dc = reinterpret_cast<const Chunk *>(prm.D) + (size_t)tile * Q3 * NCH * UNITS + tid;
-  prefetch_tile_factors(Dc - tid, (uint32_t)(NCH * UNITS * sizeof(Chunk)), nslab, tid, NT);
+  constexpr uint32_t SLAB_ROW = (uint32_t)(NCH * UNITS * sizeof(Chunk));   // one slab, all pairs
+  prefetch_factor_slabs(Dc - tid, SLAB_ROW, 0, min(l2_window_slabs((int)SLAB_ROW, Q3), nslab), tid, NT);
 #pragma unroll
   for (int s = 0; s < PDX; ++s) {
     if (has_pair && s < nslab) {

@@ -193,9 +193,14 @@ __device__ __forceinline__ void apply3d_tc_body(const ApplyParams &prm, const in
       }
     }
   };
-  // the tile's factors into L2 (the stream from DRAM then runs during staging
-  // and phases A and B; phase C's loads hit L2)
-  prefetch_tile_factors(Dc, (uint32_t)(NCH * UNITS * sizeof(Chunk)), nslab, tid, NT);
+  // the tile's first factor slabs into L2 (the stream from DRAM then runs
+  // during staging and phases A and B): the whole tile where it is small, else
+  // about 96 KB (every warp walks all slabs once per m-tile, so a rolling
+  // window per warp would not fit the block's access order)
+  {
+    constexpr uint32_t SLAB_ROW = (uint32_t)(NCH * UNITS * sizeof(Chunk));
+    prefetch_factor_slabs(Dc, SLAB_ROW, 0, min(l2_window_slabs((int)SLAB_ROW, Q3), nslab), tid, NT);
+  }
   Chunk fc[2][2][NCH];
   if (warp < NMT) load_factors(warp, 0, fc[0]);
 
