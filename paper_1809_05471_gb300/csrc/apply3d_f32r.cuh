@@ -63,6 +63,10 @@ __device__ __forceinline__ uint32_t ldg_stream(const uint32_t *p) {
   return r;
 }
 
+// Flags of the register-prefetch kernel (template parameter RL).
+constexpr int kReloadTables = 1;
+constexpr int kL2Prefetch = 2;
+
 template <int P, int S1, int S2, int S3>
 struct TileF2R {
   static constexpr int E1 = S1 + P - 1, E2 = S2 + P - 1, E3 = S3 + P - 1;
@@ -91,7 +95,7 @@ struct TileF2R {
 // NTX: block size when it is not the tile's own (0); a persistent kernel that
 // runs tiles of several orders in blocks of one size passes its block size,
 // which must cover the tile's pencil pairs.
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL, int NTX = 0>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int RL, int NTX = 0>
 __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const int tile) {
   using G = TileF2R<P, S1, S2, S3>;
   constexpr int E1 = G::E1, E2 = G::E2, E3 = G::E3;
@@ -109,6 +113,7 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
   // resident block per SM (64^3, p = 4: 61 -> 67 us).
   constexpr int SLABB = NCH * (int)sizeof(Chunk);
   constexpr int PDX = STIFF ? PD : cmin(Q3, cmax(PD, PD * 48 / SLABB));
+  constexpr bool L2P = (RL & kL2Prefetch) != 0;
 
   extern __shared__ __align__(16) unsigned char smem_f32r[];
   float *sm = reinterpret_cast<float *>(smem_f32r);
@@ -129,15 +134,17 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
   const int ke3 = min(S3, prm.K[2] - e03);
   const int nslab = ke3 * P;
 
-  // ---- the tile's factors (up to about 96 KB of them) into L2 now, as
-  // evict-first lines: the stream from DRAM runs during staging and phases A
-  // and B, and the register loads of phase C hit L2; then the first PDX slabs
-  // into registers (consumed in phase C)
+  // ---- with L2P, the tile's factors (up to about 96 KB of them) into L2 now,
+  // as evict-first lines: the stream from DRAM runs during staging and phases
+  // A and B, and the register loads of phase C hit L2; then the first PDX
+  // slabs into registers (consumed in phase C)
   const bool has_pair = tid < NPAIR;
   Chunk dq[PDX][NCH];
   const Chunk *Dc = reinterpret_cast<const Chunk *>(prm.D) + (size_t)tile * Q3 * NCH * UNITS + tid;
-  constexpr uint32_t SLAB_ROW = (uint32_t)(NCH * UNITS * sizeof(Chunk));   // one slab, all pairs
-  prefetch_factor_slabs(Dc - tid, SLAB_ROW, 0, min(l2_window_slabs((int)SLAB_ROW, Q3), nslab), tid, NT);
+  if constexpr (L2P) {
+    constexpr uint32_t SLAB_ROW = (uint32_t)(NCH * UNITS * sizeof(Chunk));   // one slab, all pairs
+    prefetch_factor_slabs(Dc - tid, SLAB_ROW, 0, min(l2_window_slabs((int)SLAB_ROW, Q3), nslab), tid, NT);
+  }
 #pragma unroll
   for (int s = 0; s < PDX; ++s) {
     if (has_pair && s < nslab) {
@@ -274,7 +281,7 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
             const float2 g1 = ffma2(D13, d3, ffma2(D12, d2, fmul2(D11, d1)));
             const float2 g2 = ffma2(D23, d3, ffma2(D22, d2, fmul2(D12, d1)));
             const float2 g3 = ffma2(D33, d3, ffma2(D23, d2, fmul2(D13, d1)));
-            if constexpr (RL) {
+            if constexpr ((RL & kReloadTables) != 0) {
               // read the tables again (volatile shared loads) instead of
               // keeping them live across the product: fewer registers
               const float4 *b4 = reinterpret_cast<const float4 *>(t3b + q3 * 2 * PP);
@@ -408,14 +415,14 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
 // Two kernel entry points per configuration: without a minimum of resident
 // blocks (the register allocator's own choice) and with one (MINB > 0 caps the
 // registers per thread at 65536 / (MINB * threads)); the launch picks by MINB.
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int RL>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
 apply3d_f32r_kernel(const ApplyParams prm) {
   pdl_allow_dependents();
   apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF, RL>(prm, blockIdx.x);
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL, int MINB>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int RL, int MINB>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT, MINB)
 apply3d_f32r_kernel_mb(const ApplyParams prm) {
   pdl_allow_dependents();
@@ -424,21 +431,21 @@ apply3d_f32r_kernel_mb(const ApplyParams prm) {
 
 // Many patches in one launch: block b works on tile b - first_block[patch] of
 // patch = block_patch[b], with that patch's parameters.
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int RL>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT)
 apply3d_f32r_batched(const BatchParams bp) {
   const int patch = bp.block_patch[blockIdx.x];
   apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF, RL>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL, int MINB>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int RL, int MINB>
 __global__ void __launch_bounds__(TileF2R<P, S1, S2, S3>::NT, MINB)
 apply3d_f32r_batched_mb(const BatchParams bp) {
   const int patch = bp.block_patch[blockIdx.x];
   apply3d_f32r_body<P, S1, S2, S3, STIFF, PD, BF, RL>(bp.params[patch], blockIdx.x - bp.first_block[patch]);
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL, int MINB>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int RL, int MINB>
 cudaError_t launch_apply3d_f32r(const ApplyParams &prm, cudaStream_t s) {
   using G = TileF2R<P, S1, S2, S3>;
   const size_t sh = G::smem_floats(STIFF) * sizeof(float);
@@ -449,7 +456,7 @@ cudaError_t launch_apply3d_f32r(const ApplyParams &prm, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, bool RL, int MINB>
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int RL, int MINB>
 cudaError_t launch_apply3d_f32r_batched(const BatchParams &bp, int blocks, cudaStream_t s) {
   using G = TileF2R<P, S1, S2, S3>;
   const size_t sh = G::smem_floats(STIFF) * sizeof(float);
@@ -460,7 +467,7 @@ cudaError_t launch_apply3d_f32r_batched(const BatchParams &bp, int blocks, cudaS
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, int PD, bool BF, bool RL, int MINB>
+template <int P, int S1, int S2, int S3, int PD, bool BF, int RL, int MINB>
 cudaError_t prepare_apply3d_f32r() {
   using G = TileF2R<P, S1, S2, S3>;
   const int sm = (int)(G::smem_floats(false) * sizeof(float));
@@ -483,9 +490,10 @@ cudaError_t prepare_apply3d_f32r() {
 
 // BF: bfloat16-stored factors. PD: slabs prefetched ahead. MINB: minimum
 // resident blocks per SM asked of the register allocator (0: its own choice).
-// RL: phase C reads the direction-3 tables again for the transposed sweep
-// instead of keeping them live across the product.
-template <int P, int S1, int S2, int S3, bool BF = false, int PD = 2, int MINB = 0, bool RL = false>
+// RL: flags; kReloadTables: phase C reads the direction-3 tables again for the
+// transposed sweep instead of keeping them live across the product;
+// kL2Prefetch: the tile requests its factors into L2 at entry.
+template <int P, int S1, int S2, int S3, bool BF = false, int PD = 2, int MINB = 0, int RL = 0>
 ApplyKernel make_apply3d_f32r() {
   using G = TileF2R<P, S1, S2, S3>;
   static_assert(G::NT <= 1024, "tile too large for one block");

@@ -5,6 +5,8 @@
 //   register prefetch, tile 8, 8, 2
 //   register prefetch, tile 8, 8, 4
 //   TMA ring, tile 16, 8, 4
+//   register prefetch, tile 2, 2, 1
+// Register-prefetch kernels request their tile's factors into L2 at entry: FP32 no, BF16 no.
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): tile 8, 8, 4, 8 warps; tile 8, 8, 2, 8 warps.
 // Factors evaluated on the fly (FP32): tile 8, 8, 2 first, then 8, 4, 4.
@@ -30,11 +32,12 @@ int apply3d_p2(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 2, true>() : make_apply3d_f32r<2, 8, 8, 2>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 4, true>() : make_apply3d_f32r<2, 8, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 2, true, 2, 0, 0>() : make_apply3d_f32r<2, 8, 8, 2, false, 2, 0, 0>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 4, true, 2, 0, 0>() : make_apply3d_f32r<2, 8, 8, 4, false, 2, 0, 0>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<2, 16, 8, 4, true>() : make_apply3d_f32<2, 16, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 2, 2, 1, true, 2, 0, 0>() : make_apply3d_f32r<2, 2, 2, 1, false, 2, 0, 0>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 2, true>() : make_apply3d_f32r<2, 8, 8, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 2, true, 2, 0, 0>() : make_apply3d_f32r<2, 8, 8, 2, false, 2, 0, 0>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 4, true>() : make_apply3d_f32r<2, 8, 8, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 16, 8, 4, true>() : make_apply3d_f32r<2, 16, 8, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 4, 8, true>() : make_apply3d_f32r<2, 8, 4, 8>();

@@ -5,6 +5,7 @@
 //   FP32: register prefetch, tile 8, 4, 4, registers capped for 4 resident blocks, tables reloaded for the transposed sweep; BF16: TMA ring, tile 8, 8, 4
 //   FP32: TMA ring, tile 8, 8, 4; BF16: register prefetch, tile 8, 4, 4
 //   register prefetch, tile 4, 4, 4
+// Register-prefetch kernels request their tile's factors into L2 at entry: FP32 yes, BF16 no.
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): tile 8, 4, 4, 6 warps; tile 4, 4, 4, 9 warps.
 // Factors evaluated on the fly (FP32): tile 8, 4, 2 first, then 4, 4, 4.
@@ -30,11 +31,11 @@ int apply3d_p3(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 4, 4, false, 2, 4, true>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 4, 4, true>() : make_apply3d_f32<3, 8, 8, 4>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 4, true>() : make_apply3d_f32r<3, 4, 4, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 4, 4, false, 2, 4, 3>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 4, 4, true, 2, 0, 0>() : make_apply3d_f32<3, 8, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 4, true, 2, 0, 0>() : make_apply3d_f32r<3, 4, 4, 4, false, 2, 0, 2>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 4, 4, false, 2, 4, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 4, 4, false, 2, 4, 3>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 4, true>() : make_apply3d_f32r<3, 4, 4, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 8, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 8, 2, true>() : make_apply3d_f32r<3, 8, 8, 2>();

@@ -5,6 +5,8 @@
 //   register prefetch, tile 4, 4, 4, registers capped for 4 resident blocks, tables reloaded for the transposed sweep
 //   TMA ring, tile 8, 4, 2
 //   TMA ring, tile 4, 4, 4
+//   register prefetch, tile 4, 4, 1
+// Register-prefetch kernels request their tile's factors into L2 at entry: FP32 no, BF16 yes.
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): tile 4, 4, 4, 8 warps; tile 4, 4, 8, 8 warps.
 // Factors evaluated on the fly (FP32): tile 4, 4, 2 first, then 4, 4, 4.
@@ -30,11 +32,12 @@ int apply3d_p4(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true, 2, 0, 2>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, 1>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 8, 4, 2, true>() : make_apply3d_f32<4, 8, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 4, 4, 4, true>() : make_apply3d_f32<4, 4, 4, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 1, true, 2, 0, 2>() : make_apply3d_f32r<4, 4, 4, 1, false, 2, 0, 0>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true, 2, 0, 2>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, 1>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 2, 4, true>() : make_apply3d_f32r<4, 4, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 8, 4, 4, true>() : make_apply3d_f32r<4, 8, 4, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 8, 4, 2, true>() : make_apply3d_f32r<4, 8, 4, 2>();

@@ -6,6 +6,7 @@
 //   register prefetch, tile 2, 2, 2, registers capped for 4 resident blocks
 //   register prefetch, tile 4, 4, 2
 //   TMA ring, tile 4, 2, 2
+// Register-prefetch kernels request their tile's factors into L2 at entry: FP32 no, BF16 no.
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): tile 2, 2, 8, 9 warps; tile 4, 2, 4, 6 warps.
 // Factors evaluated on the fly (FP32): tile 2, 2, 8 first, then 2, 2, 2.
@@ -31,12 +32,12 @@ int apply3d_p6(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 8, true, 2, 4, true>() : make_apply3d_f32r<6, 2, 2, 8, false, 2, 4, true>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 2, true>() : make_apply3d_f32r<6, 2, 2, 2, false, 2, 4, false>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 4, 2, true>() : make_apply3d_f32r<6, 4, 4, 2>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 8, true, 2, 4, 1>() : make_apply3d_f32r<6, 2, 2, 8, false, 2, 4, 1>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 2, true, 2, 0, 0>() : make_apply3d_f32r<6, 2, 2, 2, false, 2, 4, 0>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 4, 2, true, 2, 0, 0>() : make_apply3d_f32r<6, 4, 4, 2, false, 2, 0, 0>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<6, 4, 2, 2, true>() : make_apply3d_f32<6, 4, 2, 2>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 8, true, 2, 4, true>() : make_apply3d_f32r<6, 2, 2, 8, false, 2, 4, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 8, true, 2, 4, 1>() : make_apply3d_f32r<6, 2, 2, 8, false, 2, 4, 1>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 2, 2, 6, true>() : make_apply3d_f32r<6, 2, 2, 6>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 2, 4, true>() : make_apply3d_f32r<6, 4, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<6, 4, 4, 2, true>() : make_apply3d_f32r<6, 4, 4, 2>();

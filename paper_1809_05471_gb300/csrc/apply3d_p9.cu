@@ -6,6 +6,7 @@
 //   register prefetch, tile 2, 2, 8, registers capped for 2 resident blocks, tables reloaded for the transposed sweep
 //   register prefetch, tile 2, 2, 2, registers capped for 2 resident blocks, tables reloaded for the transposed sweep
 //   TMA ring, tile 2, 2, 2
+// Register-prefetch kernels request their tile's factors into L2 at entry: FP32 yes, BF16 yes.
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): tile 2, 2, 8, 7 warps; tile 2, 2, 6, 7 warps.
 // Factors evaluated on the fly (FP32): tile 2, 2, 4 first, then 2, 2, 2.
@@ -31,12 +32,12 @@ int apply3d_p9(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 6, true, 2, 2, true>() : make_apply3d_f32r<9, 2, 2, 6, false, 2, 2, true>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 8, true>() : make_apply3d_f32r<9, 2, 2, 8, false, 2, 2, true>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 2, true>() : make_apply3d_f32r<9, 2, 2, 2, false, 2, 2, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 6, true, 2, 2, 3>() : make_apply3d_f32r<9, 2, 2, 6, false, 2, 2, 3>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 8, true, 2, 0, 2>() : make_apply3d_f32r<9, 2, 2, 8, false, 2, 2, 3>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 2, true, 2, 0, 2>() : make_apply3d_f32r<9, 2, 2, 2, false, 2, 2, 3>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<9, 2, 2, 2, true>() : make_apply3d_f32<9, 2, 2, 2>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 6, true, 2, 2, true>() : make_apply3d_f32r<9, 2, 2, 6, false, 2, 2, true>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 6, true, 2, 2, 3>() : make_apply3d_f32r<9, 2, 2, 6, false, 2, 2, 3>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 8, true>() : make_apply3d_f32r<9, 2, 2, 8>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 4, true>() : make_apply3d_f32r<9, 2, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 2, true>() : make_apply3d_f32r<9, 2, 2, 2>();

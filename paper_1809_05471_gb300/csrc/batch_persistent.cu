@@ -31,7 +31,7 @@ constexpr int kPersistentMinP = 2, kPersistentMaxP = 6;
 constexpr int kPersTile[5][3] = {{8, 8, 4}, {8, 4, 4}, {4, 4, 4}, {4, 4, 4}, {2, 2, 8}};
 
 #define IGASF_PERS_BODY(P, S1, S2, S3) \
-  apply3d_f32r_body<P, S1, S2, S3, STIFF, 2, BF, true, kPersistentThreads>(prm, w.y)
+  apply3d_f32r_body<P, S1, S2, S3, STIFF, 2, BF, kReloadTables, kPersistentThreads>(prm, w.y)
 
 // One resident block per SM guaranteed to the register allocator: the tile
 // bodies of orders 5 and 6 keep about 12 (S3 + p - 1) registers of per-pencil

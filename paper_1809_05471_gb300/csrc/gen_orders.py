@@ -5,8 +5,14 @@ IGASF_TILE_SEARCH build adds, and the two on-the-fly candidates.
 
 A candidate is (variant, tile[, register cap in resident blocks[, reload[, BF16
 too]]]), variant R = register prefetch, T = TMA ring; the cap and the reload apply
-to FP32 only unless the last flag is set; ("pair", FP32 candidate, BF16 candidate)
+to FP32 only unless the last flag is set; the L2 prefetch per order and precision
+is in l2_prefetch; ("pair", FP32 candidate, BF16 candidate)
 gives the two precisions different defaults.
+
+The lists of p = 2 and 4 end with the paper's narrow macro-element shape, p x p x 1
+elements with the thin direction last (Sec. 4, narrow macro-elements), for the
+autotuner; for odd p that shape has an odd number of direction-1 points per tile,
+which the pencil-pair kernels cannot hold.
 
     python paper_1809_05471_gb300/csrc/gen_orders.py
 """
@@ -16,9 +22,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 R, T = "r", "t"
 f64 = {2: "8, 8, 8", 3: "8, 4, 4", 4: "4, 4, 4", 5: "4, 2, 2", 6: "4, 2, 2", 7: "2, 2, 2", 8: "2, 2, 2", 9: "2, 1, 2"}
 main = {
- 2: [(R, "8, 8, 2"), (R, "8, 8, 4"), (T, "16, 8, 4")],
+ 2: [(R, "8, 8, 2"), (R, "8, 8, 4"), (T, "16, 8, 4"), (R, "2, 2, 1")],
  3: [("pair", (R, "8, 4, 4", 4, 1), (T, "8, 8, 4")), ("pair", (T, "8, 8, 4"), (R, "8, 4, 4")), (R, "4, 4, 4")],
- 4: [(R, "4, 4, 4", 4, 1), (T, "8, 4, 2"), (T, "4, 4, 4")],
+ 4: [(R, "4, 4, 4", 4, 1), (T, "8, 4, 2"), (T, "4, 4, 4"), (R, "4, 4, 1")],
  5: [(T, "4, 4, 4"), (R, "4, 4, 4"), (R, "4, 2, 4")],
  6: [(R, "2, 2, 8", 4, 1, 1), (R, "2, 2, 2", 4), (R, "4, 4, 2"), (T, "4, 2, 2")],
  7: [("pair", (R, "2, 2, 6", 2, 1), (R, "2, 2, 8")), ("pair", (R, "2, 2, 8", 3, 1), (R, "2, 2, 6")),
@@ -58,6 +64,11 @@ tc = {
  8: [("2, 2, 8", 8, 2), ("2, 2, 6", 8, 2)],
  9: [("2, 2, 8", 7, 2), ("2, 2, 6", 7, 2)],
 }
+# orders whose register-prefetch kernels request their tile's factors into L2
+# at entry (kL2Prefetch), per precision: where the order sweep measured a gain
+# (FP32 p = 3: 0.244 -> 0.215 ms; BF16 p = 4: 0.436 -> 0.385 ms; 2 to 7 % at
+# p = 7..9); off at the bench cube's p = 4 FP32, where it slowed the gather
+l2_prefetch = {"fp32": {3, 7, 8, 9}, "bf16": {4, 7, 8, 9}}
 mk = {R: "make_apply3d_f32r", T: "make_apply3d_f32"}
 name = {R: "register prefetch", T: "TMA ring"}
 for P in range(2, 10):
@@ -75,6 +86,9 @@ for P in range(2, 10):
             L.append("//   FP32: %s; BF16: %s" % (describe(c[1]), describe(c[2])))
         else:
             L.append("//   %s" % describe(c))
+    L.append("// Register-prefetch kernels request their tile's factors into L2 at entry: "
+             "FP32 %s, BF16 %s." % ("yes" if P in l2_prefetch["fp32"] else "no",
+                                   "yes" if P in l2_prefetch["bf16"] else "no"))
     L.append("// IGASF_TILE_SEARCH compiles every listed shape in both variants.")
     L.append("// Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): %s." % "; ".join(
         "tile %s, %d warps" % (t, w) for t, w, _ in tc[P]))
@@ -91,19 +105,22 @@ for P in range(2, 10):
     L.append("  const bool bf = prec == IGASF_BF16;")
     L.append("#ifndef IGASF_TILE_SEARCH")
     def inst(c):
-        """(BF16, FP32) instantiations of a candidate (variant, tile[, minb[, reload]])."""
+        """(BF16, FP32) instantiations of a candidate (variant, tile[, minb[, reload[, BF16 too]]])."""
         v, t = c[0], c[1]
         minb = c[2] if len(c) > 2 else 0
-        rl = "true" if len(c) > 3 and c[3] else "false"
-        if v == R and (minb or rl == "true") and len(c) > 4 and c[4]:
-            return ("%s<%d, %s, true, 2, %d, %s>()" % (mk[v], P, t, minb, rl),
-                    "%s<%d, %s, false, 2, %d, %s>()" % (mk[v], P, t, minb, rl))
-        if v == R and (minb or rl == "true"):
-            # BF16 keeps the compiler's register choice and the tables in registers
-            # (measured faster for the bfloat16 stream at these orders)
-            return ("%s<%d, %s, true>()" % (mk[v], P, t),
-                    "%s<%d, %s, false, 2, %d, %s>()" % (mk[v], P, t, minb, rl))
-        if v == T and rl == "true":
+        reload = bool(len(c) > 3 and c[3])
+        if v == R:
+            f32 = (1 if reload else 0) | (2 if P in l2_prefetch["fp32"] else 0)
+            if len(c) > 4 and c[4]:
+                mb16, f16 = minb, (1 if reload else 0)
+            else:
+                # BF16 keeps the compiler's register choice and the tables in registers
+                # (measured faster for the bfloat16 stream at these orders)
+                mb16, f16 = 0, 0
+            f16 |= 2 if P in l2_prefetch["bf16"] else 0
+            return ("%s<%d, %s, true, 2, %d, %d>()" % (mk[v], P, t, mb16, f16),
+                    "%s<%d, %s, false, 2, %d, %d>()" % (mk[v], P, t, minb, f32))
+        if reload:
             return ("%s<%d, %s, true, true>()" % (mk[v], P, t), "%s<%d, %s, false, true>()" % (mk[v], P, t))
         return ("%s<%d, %s, true>()" % (mk[v], P, t), "%s<%d, %s>()" % (mk[v], P, t))
     def inst2(c):
