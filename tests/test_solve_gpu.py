@@ -61,3 +61,32 @@ def test_cg_is_deterministic_and_reports_non_convergence():
         x3 = torch.zeros_like(b)
         r3 = plan.cg_solve(b, x3, inner_prec=G.FP64, rtol=1e-10, max_iterations=3)
         assert not r3["converged"] and r3["inner_iterations"] == 3
+
+
+def test_refined_solve_of_the_solver_workload_shape_checked_by_oracle_rows():
+    """The solver workload's shape at half its size (p = 5, 48^3 elements, the
+    perturbed cube, a = 1, homogeneous Dirichlet) with FP32 and TF32 inner
+    solves in FP64 refinement to 1e-10: on sampled interior rows the oracle's
+    residual b_m - (K x)_m, with K from the definition, is within the solve's
+    own bound (each |r_m| <= ||r||_2 <= 1e-10 ||b||_2) plus the FP64 rounding of
+    the two operators (1e-13 ||K||_inf ||x||_inf)."""
+    import torch
+    patch, _ = I.make_patch(3, 5, 48, noise_amp=0.2 / 48, seed=0)
+    m = _interior_mask(patch)
+    rng = np.random.default_rng(11)
+    b = rng.uniform(-1, 1, patch.num_dofs)
+    b[~m] = 0.0
+    idx = np.flatnonzero(m)
+    rows = np.sort(rng.choice(idx, 32, replace=False))
+    with G.Plan.from_patch(patch, precisions=(G.FP64, G.FP32, G.TF32)) as plan:
+        bd = torch.as_tensor(b, device="cuda")
+        for inner in (G.FP32, G.TF32):
+            xd = torch.zeros_like(bd)
+            rep = plan.cg_solve(bd, xd, inner_prec=inner, rtol=1e-10, inner_rtol=1e-4)
+            assert rep["converged"] and rep["final_relres"] <= 1e-10, (inner, rep)
+            x = xd.cpu().numpy()
+            assert np.all(x[~m] == 0.0)
+            kx, ra = O.apply_rows(patch, O.STIFFNESS, x, rows)
+            r = b[rows] - kx
+            bound = 1e-10 * np.linalg.norm(b) + 1e-13 * ra.max() * np.max(np.abs(x))
+            assert np.max(np.abs(r)) <= bound, (inner, np.max(np.abs(r)), bound)
