@@ -467,11 +467,14 @@ def run_igasf(args):
     N, Qtot = plan.num_dofs, plan.num_quad_points
     fp64_tf = fp64_peak() if extras else None
 
-    def roofline(op, prec, kernel_ms, Qt, Nd, pp, KK, dd=3):
+    def roofline(op, prec, kernel_ms, Qt, Nd, pp, KK, dd=3, cube=True):
+        """cube: the bench cube's own launch, whose DRAM traffic a committed ncu
+        summary may record (the order sweep's launches have none)."""
         ab = algorithmic_bytes(op, prec, Qt, Nd, dd)
         ach = ab / (kernel_ms * 1e-3) / 1e9
+        traffic = traffic_record("%s_%s_p%d_cube%d" % (op, prec, pp, KK)) if cube else None
         r = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-             "frac": round(ach / hbm, 4), "traffic": traffic_record("%s_%s_p%d" % (op, prec, pp)),
+             "frac": round(ach / hbm, 4), "traffic": traffic,
              "algorithmic_bytes_per_launch": ab, "kernel_ms": round(kernel_ms, 5),
              "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src}
         if prec == "fp64":
@@ -633,7 +636,7 @@ def order_sweep(orders, G, I, O, torch, stream, roofline):
                           "tile": plan.describe(pc[prec])["tile"],
                           "value": round(N / (ms / steps * 1e-3) / 1e9, 4),
                           "ms_per_step": round(ms / steps, 5), "steps": steps,
-                          "roofline": roofline("stiffness", prec, k_ms, Q, N, p, K),
+                          "roofline": roofline("stiffness", prec, k_ms, Q, N, p, K, cube=False),
                           "gather_ms": round(g_ms, 5), "setup_s": round(setup_s, 3)})
             plan.close()
             del ud, vd
