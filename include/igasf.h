@@ -210,6 +210,21 @@ int igasf_apply_prec(igasf_handle h, int op, int prec, const void *u, void *v, v
 int igasf_apply_host(igasf_handle h, int op, int prec, const void *u_host, void *v_host,
                      void *stream);
 
+/*
+ * As igasf_apply_host, but asynchronous, for applying the operator to a
+ * sequence of host vectors: enqueues the copy of u_host to one of two device
+ * input buffers (alternating from call to call) on a copy stream of the plan,
+ * the apply on `stream` once that copy has landed, and the result into v_host
+ * (written by the gather through the device mapping of a page-locked v_host,
+ * else copied back from a staging buffer on `stream`), and returns. The copy of
+ * call k + 1 runs while call k's apply executes. v_host is valid, and u_host and
+ * v_host may be reused or freed, only after `stream` has been synchronised. The
+ * two input buffers and the copy stream are created at setup. Errors: as
+ * igasf_apply_host.
+ */
+int igasf_apply_host_async(igasf_handle h, int op, int prec, const void *u_host, void *v_host,
+                           void *stream);
+
 /* Synchronise the device and free everything the handle owns. NULL is a no-op. */
 int igasf_destroy(igasf_handle h);
 

@@ -44,6 +44,11 @@ void destroy_events(igasf_plan *h) {
 void free_plan(igasf_plan *h) {
   if (!h) return;
   destroy_events(h);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
+    if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);
+  }
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   cudaFree(h->status);
   cudaFree(h->ctrl64);
   cudaFree(h->dinv64);
@@ -68,6 +73,7 @@ void free_plan(igasf_plan *h) {
     cudaFree(v.ctrl32);
     cudaFree(v.vpart);
     cudaFree(v.u_stage);
+    cudaFree(v.u_stage2);
     cudaFree(v.v_stage);
   }
   delete h;
@@ -309,6 +315,11 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
   h->coef_constant = c.constant;
   h->coef_alpha = c.alpha;
   TRY_CUDA(cudaGetDevice(&h->device), "cudaGetDevice");
+  TRY_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
+  for (int i = 0; i < 2; ++i) {
+    TRY_CUDA(cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming), "events");
+    TRY_CUDA(cudaEventCreateWithFlags(&h->ev_free[i], cudaEventDisableTiming), "events");
+  }
   TRY(alloc((void **)&h->status, sizeof(unsigned int), "status word"));
   TRY_CUDA(cudaMemset(h->status, 0, sizeof(unsigned int)), "status word");
   h->Ntot = 1;
@@ -411,6 +422,7 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     v.vpart_bytes = (size_t)v.ntiles * vol * es;
     TRY(alloc(&v.vpart, v.vpart_bytes, "workspace"));
     TRY(alloc(&v.u_stage, (size_t)h->Ntot * es, "staging"));
+    TRY(alloc(&v.u_stage2, (size_t)h->Ntot * es, "staging"));
     TRY(alloc(&v.v_stage, (size_t)h->Ntot * es, "staging"));
     TRY_CUDA(v.k.prepare(), "kernel attributes");
     if (!v.on_the_fly) g.out[g.nout++] = v.L;
@@ -535,6 +547,40 @@ int igasf_apply_host(igasf_handle h, int op, int prec, const void *u_host, void 
   }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return IGASF_OK;
+}
+
+int igasf_apply_host_async(igasf_handle h, int op, int prec, const void *u_host, void *v_host,
+                           void *stream) {
+  if (!h) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL");
+  if (prec < 0 || prec >= kNumPrec || !h->var[prec].present)
+    return fail(IGASF_ERR_UNSUPPORTED, "precision %d was not stored at setup", prec);
+  if (!u_host || !v_host) return fail(IGASF_ERR_INVALID_ARG, "u and v must be non-NULL");
+  Variant &var = h->var[prec];
+  const size_t bytes = (size_t)h->Ntot * prec_size(prec);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int b = h->stage_next;
+  void *ub = b ? var.u_stage2 : var.u_stage;
+  // the copy into buffer b waits for the apply that last read it (two calls ago),
+  // runs on the copy stream (overlapping the previous call's apply), and the apply
+  // waits for the copy
+  cudaError_t e = cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ub, u_host, bytes, cudaMemcpyHostToDevice, h->copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_copied[b], h->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_copied[b], 0);
+  if (e != cudaSuccess) return cuda_fail(e, "copy u to the device");
+  cudaPointerAttributes at;
+  void *v_dev = nullptr;
+  if (cudaPointerGetAttributes(&at, v_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer != nullptr && ((uintptr_t)at.devicePointer % prec_size(prec)) == 0)
+    v_dev = at.devicePointer;
+  cudaGetLastError();   // a pageable pointer may leave an error from the attribute query
+  int rc = igasf_apply_prec(h, op, prec, ub, v_dev ? v_dev : var.v_stage, stream);
+  if (rc != IGASF_OK) return rc;
+  e = cudaEventRecord(h->ev_free[b], s);
+  if (e == cudaSuccess && !v_dev) e = cudaMemcpyAsync(v_host, var.v_stage, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "order the host-buffer apply");
+  h->stage_next = b ^ 1;
   return IGASF_OK;
 }
 

@@ -23,6 +23,7 @@ struct Variant {
   void *vpart = nullptr;
   size_t vpart_bytes = 0;
   void *u_stage = nullptr, *v_stage = nullptr;
+  void *u_stage2 = nullptr;                 // second input buffer of igasf_apply_host_async
   int2 *gtab[kMaxDim] = {nullptr, nullptr, nullptr};   // gather tables, see gather_table
   // factors evaluated on the fly (FP32 only): no stored factors
   bool on_the_fly = false;
@@ -50,6 +51,11 @@ struct igasf_plan {
   int skip_slab = -1;                    // test hook, see igasf_set_test_fault
   std::vector<cudaEvent_t> prof_events;  // 3 per timed apply
   int prof_next = 0;                     // applies recorded so far
+  // igasf_apply_host_async: copies into the two input buffers run on their own
+  // stream, ordered against the applies by events
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  int stage_next = 0;
   double *dinv64 = nullptr;              // inverse Jacobi diagonal of K (solver), lazily
   float *dinv32 = nullptr;
   int coef_kind = IGASF_COEF_CONSTANT;   // for factors evaluated on the fly

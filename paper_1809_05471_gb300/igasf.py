@@ -45,7 +45,8 @@ ERRORS = {
 
 # every symbol include/igasf.h declares
 EXPORTED = [
-    "igasf_setup", "igasf_apply", "igasf_apply_prec", "igasf_apply_host", "igasf_destroy",
+    "igasf_setup", "igasf_apply", "igasf_apply_prec", "igasf_apply_host", "igasf_apply_host_async",
+    "igasf_destroy",
     "igasf_num_dofs", "igasf_num_quad_points", "igasf_describe", "igasf_get_tables",
     "igasf_get_factors", "igasf_quad_points", "igasf_profile_begin", "igasf_profile_end", "igasf_apply_noalloc",
     "igasf_device_status", "igasf_set_test_fault", "igasf_cg_solve",
@@ -106,6 +107,7 @@ def load_library(path: str = LIB_PATH):
     lib.igasf_apply.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.igasf_apply_prec.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     lib.igasf_apply_host.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+    lib.igasf_apply_host_async.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     lib.igasf_destroy.argtypes = [vp]
     lib.igasf_num_dofs.argtypes = [vp]
     lib.igasf_num_dofs.restype = ctypes.c_int64
@@ -238,6 +240,15 @@ class Plan:
         vp = v.ctypes.data if isinstance(v, np.ndarray) else v.data_ptr()
         _check(load_library().igasf_apply_host(self._h(), int(op), int(prec), up, vp,
                                                _stream_handle(stream)))
+        return v
+
+    def apply_host_async(self, op: int, u, v, prec: int = FP64, stream=None):
+        """Enqueue v = A u for host arrays (pinned CPU tensors or numpy arrays);
+        v is valid after the stream is synchronised."""
+        up = u.ctypes.data if isinstance(u, np.ndarray) else u.data_ptr()
+        vp = v.ctypes.data if isinstance(v, np.ndarray) else v.data_ptr()
+        _check(load_library().igasf_apply_host_async(self._h(), int(op), int(prec), up, vp,
+                                                     _stream_handle(stream)))
         return v
 
     def describe(self, prec: int = FP64) -> dict:

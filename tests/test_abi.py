@@ -172,6 +172,7 @@ def test_null_handle_calls(lib):
     assert lib.igasf_apply(None, 0, None, None, None) == -1
     assert lib.igasf_apply_prec(None, 0, 0, None, None, None) == -1
     assert lib.igasf_apply_host(None, 0, 0, None, None, None) == -1
+    assert lib.igasf_apply_host_async(None, 0, 0, None, None, None) == -1
     assert lib.igasf_destroy(None) == 0
     assert lib.igasf_num_dofs(None) == -1
     assert lib.igasf_num_quad_points(None) == -1
