@@ -171,8 +171,11 @@ typedef struct {
  *   orders       host, d ints: order p per direction (all equal, 2..IGASF_MAX_ORDER).
  *   knot_lengths host, d ints: entries of each knot vector.
  *   knots        host, d pointers to non-decreasing open knot vectors (first and
- *                last knot repeated p times). The GPU path needs simple interior
- *                knots (multiplicity 1); repeated ones give IGASF_ERR_UNSUPPORTED.
+ *                last knot repeated p times, interior knots at most p - 1 times:
+ *                C^(p-1-m) continuity at a knot of multiplicity m, Sec. 2). The
+ *                elements are the non-empty knot spans (Sec. 3); internally the
+ *                empty spans of repeated knots are kept as elements of zero
+ *                weight, so that the tile kernels see the simple-knot numbering.
  *   ctrl         host, N*d doubles: control point n at ctrl[n*d .. n*d+d-1].
  *   coef         host, may be NULL (= constant 1).
  *   opt          host, may be NULL (= defaults).
@@ -229,17 +232,19 @@ int igasf_apply_host_async(igasf_handle h, int op, int prec, const void *u_host,
 int igasf_destroy(igasf_handle h);
 
 int64_t igasf_num_dofs(igasf_handle h);          /* -1 on a NULL handle */
-int64_t igasf_num_quad_points(igasf_handle h);   /* -1 on a NULL handle */
+int64_t igasf_num_quad_points(igasf_handle h);   /* p^d per element (non-empty span); -1 on a NULL handle */
 
 /* Plan description for one stored precision. */
 int igasf_describe(igasf_handle h, int prec, igasf_plan_desc *out);
 
 /*
  * Univariate tables of direction `dir` (0-based) as computed on the device, in
- * FP64 (Sec. 6.1): nodes[Q], weights[Q], B[Q*p], dB[Q*p] with Q = K*p, where
- * B[q*p + j] is the value of the j-th function active on the element of
- * quadrature point q (function index = element index + j for simple knots) and
- * dB its derivative. Host outputs; any may be NULL. Synchronous.
+ * FP64 (Sec. 6.1): nodes[Q], weights[Q], B[Q*p], dB[Q*p] with Q = K*p, K the
+ * number of non-empty knot spans of the direction, where B[q*p + j] is the
+ * value of the j-th function active on the element of quadrature point q
+ * (function index = k - p + 1 + j for the element's span [t_k, t_k+1), 0-based
+ * knots; element index + j for simple knots) and dB its derivative. Host
+ * outputs; any may be NULL. Synchronous.
  */
 int igasf_get_tables(igasf_handle h, int dir, double *nodes, double *weights, double *B,
                      double *dB);

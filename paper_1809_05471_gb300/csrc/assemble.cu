@@ -2,11 +2,16 @@
 // device by sum factorization over the whole patch (Sec. 3.1, Alg. 1, with
 // eq. recursive-step1 applied to one direction after the other).
 //
-// Notation: direction a has N_a functions, K_a elements and Q_a = K_a p Gauss
-// points; function m of a direction is non-zero on the elements m - p + 1..m,
-// so a pair (m, n) of one direction can interact only for |m - n| <= p - 1.
-// Columns of a row are addressed by offsets o = n - m + p - 1 in [0, W), W =
-// 2p - 1, per direction. Term t of the bilinear form pairs the test function
+// Notation: direction a has N_a functions, K_a elements (knot spans, empty
+// ones of repeated knots included) and Q_a = K_a p Gauss points; function m of
+// a direction is non-zero on the elements m - p + 1..m, so a pair (m, n) of
+// one direction can interact only for |m - n| <= p - 1. Columns of a row are
+// addressed by offsets o = n - m + p - 1 in [0, W), W = 2p - 1, per direction.
+// The pattern holds the pairs that share a non-empty element in every
+// direction (Sec. 3, Cor. 3 and its nnz count); per direction and row m these
+// are the n of an interval [lo_a(m), lo_a(m) + cnt_a(m) - 1], since the shared
+// elements of (m, n) shrink as |m - n| grows. Empty elements have zero
+// tables, so pairs outside the pattern would only have received zeros. Term t of the bilinear form pairs the test function
 // psi_m, differentiated (or not) per direction, with the trial function phi_n
 // and one stored factor F_t = w F_ij (weights folded in). Mass: one term, no
 // derivatives, F = w |det J|. Stiffness: the d^2 terms (i, j), derivative of
@@ -213,27 +218,35 @@ __global__ void level2_kernel(const AsmDims g, const double *L1, int QC, double 
 // ---- CSR addressing -------------------------------------------------------------
 struct CsrDims {
   const int64_t *pre[3];   // prefix sums of the per-direction column counts, N_a + 1 each
+  const int *lo[3];        // first column of each row, per direction
 };
 
-__device__ __forceinline__ int count_1d(int m, int N, int p) {
-  return min(m + p - 1, N - 1) - max(m - p + 1, 0) + 1;
+__device__ __forceinline__ int count_1d(const CsrDims &c, int a, int m) {
+  return (int)(c.pre[a][m + 1] - c.pre[a][m]);
+}
+
+// is column n of direction a in the pattern of row m
+__device__ __forceinline__ bool in_pattern_1d(const CsrDims &c, int a, int m, int n) {
+  const int lo = c.lo[a][m];
+  return n >= lo && n < lo + count_1d(c, a, m);
 }
 
 __device__ __forceinline__ int64_t row_start(const AsmDims &g, const CsrDims &c, const int *m) {
   const int64_t T1 = c.pre[0][g.N[0]];
-  if (g.d == 2) return c.pre[1][m[1]] * T1 + (int64_t)count_1d(m[1], g.N[1], g.p) * c.pre[0][m[0]];
+  if (g.d == 2) return c.pre[1][m[1]] * T1 + (int64_t)count_1d(c, 1, m[1]) * c.pre[0][m[0]];
   const int64_t T2 = c.pre[1][g.N[1]];
   return c.pre[2][m[2]] * T2 * T1 +
-         (int64_t)count_1d(m[2], g.N[2], g.p) *
-             (c.pre[1][m[1]] * T1 + (int64_t)count_1d(m[1], g.N[1], g.p) * c.pre[0][m[0]]);
+         (int64_t)count_1d(c, 2, m[2]) *
+             (c.pre[1][m[1]] * T1 + (int64_t)count_1d(c, 1, m[1]) * c.pre[0][m[0]]);
 }
 
 // position of column offset o within row m (columns ascending = last direction slowest)
-__device__ __forceinline__ int64_t rank_in_row(const AsmDims &g, const int *m, const int *o) {
+__device__ __forceinline__ int64_t rank_in_row(const AsmDims &g, const CsrDims &c, const int *m,
+                                               const int *o) {
   int64_t r = 0;
   for (int a = g.d - 1; a >= 0; --a) {
-    const int lo = max(0, g.p - 1 - m[a]);
-    r = r * count_1d(m[a], g.N[a], g.p) + (o[a] - lo);
+    const int olo = c.lo[a][m[a]] - m[a] + g.p - 1;
+    r = r * count_1d(c, a, m[a]) + (o[a] - olo);
   }
   return r;
 }
@@ -260,19 +273,19 @@ __global__ void csr_structure_kernel(const AsmDims g, const CsrDims c, int64_t *
   int64_t col = 0, stride = 1;
   for (int a = 0; a < g.d; ++a) {
     const int n = m[a] + o[a] - (g.p - 1);
-    if (n < 0 || n >= g.N[a]) return;
+    if (!in_pattern_1d(c, a, m[a], n)) return;
     col += n * stride;
     stride *= g.N[a];
   }
   const int64_t start = row_start(g, c, m);
-  colind[start + rank_in_row(g, m, o)] = col;
+  colind[start + rank_in_row(g, c, m, o)] = col;
   bool first = true;
-  for (int a = 0; a < g.d; ++a) first = first && o[a] == max(0, g.p - 1 - m[a]);
+  for (int a = 0; a < g.d; ++a) first = first && m[a] + o[a] - (g.p - 1) == c.lo[a][m[a]];
   if (first) {
     rowptr[idx / Wd] = start;
     if (idx / Wd == Ntot - 1) {
       int64_t cnt = 1;
-      for (int a = 0; a < g.d; ++a) cnt *= count_1d(m[a], g.N[a], g.p);
+      for (int a = 0; a < g.d; ++a) cnt *= count_1d(c, a, m[a]);
       rowptr[Ntot] = start + cnt;
     }
   }
@@ -299,10 +312,8 @@ __global__ void last_level_kernel(const AsmDims g, const CsrDims c, const double
     m[b] = (int)(t % g.N[b]);
     t /= g.N[b];
   }
-  for (int b = 0; b < g.d; ++b) {
-    const int n = m[b] + o[b] - (p - 1);
-    if (n < 0 || n >= g.N[b]) return;
-  }
+  for (int b = 0; b < g.d; ++b)
+    if (!in_pattern_1d(c, b, m[b], m[b] + o[b] - (p - 1))) return;
   const int nL = m[a] + o[a] - (p - 1);
   int lo, hi;
   common_elements(g, a, m[a], nL, e0, e1 - 1, lo, hi);
@@ -313,10 +324,35 @@ __global__ void last_level_kernel(const AsmDims g, const CsrDims c, const double
     s += contract(g, a, (gg & 2) != 0 && g.stiff, (gg & 1) != 0 && g.stiff, m[a], o[a], lo, hi, x,
                   inner, e0 * p);
   }
-  values[row_start(g, c, m) + rank_in_row(g, m, o)] += s;
+  values[row_start(g, c, m) + rank_in_row(g, c, m, o)] += s;
 }
 
 unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// Columns of every row of direction a: lo[m] and the count; returns their sum.
+// Column n belongs to row m when an element e in [max(m, n) - p + 1, min(m, n)]
+// is non-empty.
+int64_t pattern_1d(const igasf_plan *h, int a, std::vector<int> &lo, std::vector<int> &cnt) {
+  const int p = h->p, N = h->N[a], K = h->K[a];
+  const std::vector<unsigned char> &ne = h->nonempty[a];
+  auto shares = [&](int m, int n) {
+    for (int e = std::max(std::max(m, n) - p + 1, 0); e <= std::min(std::min(m, n), K - 1); ++e)
+      if (ne[e]) return true;
+    return false;
+  };
+  lo.assign(N, 0);
+  cnt.assign(N, 0);
+  int64_t total = 0;
+  for (int m = 0; m < N; ++m) {
+    int a0 = m, b0 = m;
+    while (a0 - 1 >= std::max(m - p + 1, 0) && shares(m, a0 - 1)) --a0;
+    while (b0 + 1 <= std::min(m + p - 1, N - 1) && shares(m, b0 + 1)) ++b0;
+    lo[m] = a0;
+    cnt[m] = b0 - a0 + 1;
+    total += cnt[m];
+  }
+  return total;
+}
 
 }  // namespace
 }  // namespace igasf
@@ -325,7 +361,8 @@ extern "C" int64_t igasf_assembled_nnz(igasf_handle h) {
   using namespace igasf;
   if (!h) return set_error(IGASF_ERR_INVALID_ARG, "handle is NULL");
   int64_t nnz = 1;
-  for (int a = 0; a < h->d; ++a) nnz *= (int64_t)(2 * h->p - 1) * h->K[a] + (int64_t)(h->p - 1) * (h->p - 1);
+  std::vector<int> lo, cnt;
+  for (int a = 0; a < h->d; ++a) nnz *= pattern_1d(h, a, lo, cnt);
   return nnz;
 }
 
@@ -361,17 +398,22 @@ extern "C" int igasf_assemble_csr(igasf_handle h, int op, int64_t *rowptr, int64
   const int d = h->d, p = h->p, W = g.W, L = d - 1;
   const int Qmid = d == 3 ? g.Q[1] : 1;
 
-  // per-direction prefix sums of the column counts (host, then device)
+  // per-direction first columns and prefix sums of the column counts (host, then device)
   std::vector<int64_t> pre_h;
-  size_t pre_off[3] = {0, 0, 0};
+  std::vector<int> lo_h;
+  size_t pre_off[3] = {0, 0, 0}, lo_off[3] = {0, 0, 0};
   for (int a = 0; a < d; ++a) {
+    std::vector<int> lo, cnt;
+    pattern_1d(h, a, lo, cnt);
     pre_off[a] = pre_h.size();
+    lo_off[a] = lo_h.size();
     int64_t acc = 0;
     pre_h.push_back(0);
     for (int m = 0; m < g.N[a]; ++m) {
-      acc += std::min(m + p - 1, g.N[a] - 1) - std::max(m - p + 1, 0) + 1;
+      acc += cnt[m];
       pre_h.push_back(acc);
     }
+    lo_h.insert(lo_h.end(), lo.begin(), lo.end());
   }
   // chunk size: element layers of the last direction whose levels fit the limit
   const int64_t inner1 = (int64_t)g.N[0] * W;
@@ -383,6 +425,7 @@ extern "C" int igasf_assemble_csr(igasf_handle h, int op, int64_t *rowptr, int64
   const int64_t QCmax = (int64_t)layers * p;
 
   int64_t *pre_d = nullptr;
+  int *lo_d = nullptr;
   double *Fc = nullptr, *L1 = nullptr, *L2 = nullptr, *PT = nullptr;
   size_t pt_off[3] = {0, 0, 0}, pt_total = 0;
   for (int a = 0; a < d; ++a) {
@@ -390,6 +433,7 @@ extern "C" int igasf_assemble_csr(igasf_handle h, int op, int64_t *rowptr, int64
     pt_total += (size_t)4 * g.N[a] * W * p * p;
   }
   cudaError_t e = cudaMalloc((void **)&pre_d, sizeof(int64_t) * pre_h.size());
+  if (e == cudaSuccess) e = cudaMalloc((void **)&lo_d, sizeof(int) * lo_h.size());
   if (e == cudaSuccess) e = cudaMalloc((void **)&PT, sizeof(double) * pt_total);
   if (e == cudaSuccess) e = cudaMalloc((void **)&Fc, sizeof(double) * g.nf * QCmax * Qmid * g.Q[0]);
   if (e == cudaSuccess) e = cudaMalloc((void **)&L1, sizeof(double) * g.nterms * QCmax * Qmid * inner1);
@@ -397,6 +441,7 @@ extern "C" int igasf_assemble_csr(igasf_handle h, int op, int64_t *rowptr, int64
   auto release = [&]() {
     cudaFree(PT);
     cudaFree(pre_d);
+    cudaFree(lo_d);
     cudaFree(Fc);
     cudaFree(L1);
     cudaFree(L2);
@@ -407,8 +452,13 @@ extern "C" int igasf_assemble_csr(igasf_handle h, int op, int64_t *rowptr, int64
                      (std::string("assembly workspace: ") + cudaGetErrorString(e)).c_str());
   }
   e = cudaMemcpyAsync(pre_d, pre_h.data(), sizeof(int64_t) * pre_h.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(lo_d, lo_h.data(), sizeof(int) * lo_h.size(), cudaMemcpyHostToDevice, s);
   CsrDims c;
-  for (int a = 0; a < 3; ++a) c.pre[a] = a < d ? pre_d + pre_off[a] : nullptr;
+  for (int a = 0; a < 3; ++a) {
+    c.pre[a] = a < d ? pre_d + pre_off[a] : nullptr;
+    c.lo[a] = a < d ? lo_d + lo_off[a] : nullptr;
+  }
   int64_t Ntot = 1, Wd = 1;
   for (int a = 0; a < d; ++a) {
     Ntot *= g.N[a];

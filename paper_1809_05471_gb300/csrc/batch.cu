@@ -220,7 +220,7 @@ int igasf_batch_create_ex(int nplans, const igasf_handle *plans, int op, int pre
     const Variant &v = h->var[prec];
     b->offset[i] = off;
     off += h->Ntot;
-    b->total_qp += h->Qtot;
+    b->total_qp += h->Qapi;
     b->factor_bytes += op == IGASF_MASS ? v.bytesM : v.bytesK;
     // group by kernel
     int gi = -1;

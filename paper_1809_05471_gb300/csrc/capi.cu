@@ -81,7 +81,40 @@ void free_plan(igasf_plan *h) {
 
 size_t prec_size(int prec) { return vector_bytes(prec); }
 
-// Validate one open knot vector; count elements. Returns IGASF_OK or an error.
+// Position in the plan's full quadrature grid (all spans) of the API's
+// quadrature point q = (q_3 Qe_2 + q_2) Qe_1 + q_1 (non-empty spans only).
+int64_t full_qp_index(const igasf_plan *h, int64_t q) {
+  int64_t full = 0, stride = 1;
+  for (int a = 0; a < h->d; ++a) {
+    const int64_t Qe = (int64_t)h->Ke[a] * h->p;
+    const int qa = (int)(q % Qe);
+    q /= Qe;
+    full += ((int64_t)h->elem[a][qa / h->p] * h->p + qa % h->p) * stride;
+    stride *= h->Q[a];
+  }
+  return full;
+}
+
+// Per-point data with nc components: the API's points out of the full grid,
+// and back (the points of empty spans get zeros).
+void compact_qp(const igasf_plan *h, const double *full, double *api, int nc) {
+  for (int64_t q = 0; q < h->Qapi; ++q) {
+    const int64_t f = full_qp_index(h, q);
+    for (int c = 0; c < nc; ++c) api[q * nc + c] = full[f * nc + c];
+  }
+}
+
+void expand_qp(const igasf_plan *h, const double *api, double *full, int nc) {
+  std::fill(full, full + h->Qtot * nc, 0.0);
+  for (int64_t q = 0; q < h->Qapi; ++q) {
+    const int64_t f = full_qp_index(h, q);
+    for (int c = 0; c < nc; ++c) full[f * nc + c] = api[q * nc + c];
+  }
+}
+
+// Validate one open knot vector (interior multiplicity at most p - 1); count
+// its elements, the knot spans k = p-1 .. nk-p-1 with empty ones included.
+// Returns IGASF_OK or an error.
 int check_knots(int dir, int p, int nk, const double *t, int *K_out) {
   if (!t) return fail(IGASF_ERR_INVALID_ARG, "knots[%d] is NULL", dir);
   if (nk < 2 * p) return fail(IGASF_ERR_KNOTS, "knot vector %d has %d entries, needs >= %d", dir, nk, 2 * p);
@@ -101,9 +134,6 @@ int check_knots(int dir, int p, int nk, const double *t, int *K_out) {
     int m = 1;
     while (i + m < nk - p && t[i + m] == t[i]) ++m;
     if (m >= p) return fail(IGASF_ERR_KNOTS, "knot vector %d: interior multiplicity %d >= order %d", dir, m, p);
-    if (m > 1)
-      return fail(IGASF_ERR_UNSUPPORTED,
-                  "knot vector %d: repeated interior knot (multiplicity %d); the GPU path needs simple knots", dir, m);
     i += m;
   }
   K = nk - 2 * p + 1;
@@ -331,6 +361,19 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     h->Ntot *= h->N[a];
     h->Qtot *= h->Q[a];
   }
+  h->Qapi = 1;
+  for (int a = 0; a < d; ++a) {
+    const double *t = knots[a];
+    h->nonempty[a].assign(K[a], 0);
+    for (int e = 0; e < K[a]; ++e)
+      if (t[p + e] > t[p - 1 + e]) {
+        h->nonempty[a][e] = 1;
+        h->elem[a].push_back(e);
+      }
+    h->Ke[a] = (int)h->elem[a].size();
+    h->Qapi *= (int64_t)h->Ke[a] * p;
+    if (h->Ke[a] != K[a]) h->empty_spans = true;
+  }
   cudaStream_t s = nullptr;
   // knots, spans, tables
   for (int a = 0; a < d; ++a) {
@@ -438,8 +481,16 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
   };
   cudaError_t ce = cudaMemcpy(ctrl_d, ctrl, sizeof(double) * h->Ntot * d, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess && c.kind == IGASF_COEF_VALUES) {
+    // the caller's values belong to the non-empty spans' points
+    std::vector<double> full;
+    const double *src = c.values;
+    if (h->empty_spans) {
+      full.resize((size_t)h->Qtot);
+      expand_qp(h, c.values, full.data(), 1);
+      src = full.data();
+    }
     ce = cudaMalloc((void **)&coef_d, sizeof(double) * h->Qtot);
-    if (ce == cudaSuccess) ce = cudaMemcpy(coef_d, c.values, sizeof(double) * h->Qtot, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(coef_d, src, sizeof(double) * h->Qtot, cudaMemcpyHostToDevice);
   }
   if (ce == cudaSuccess) ce = cudaMalloc((void **)&bad_d, sizeof(unsigned int));
   if (ce == cudaSuccess) ce = cudaMemset(bad_d, 0, sizeof(unsigned int));
@@ -657,7 +708,7 @@ int igasf_set_test_fault(igasf_handle h, int skip_slab, long long wait_limit_cyc
 
 int64_t igasf_num_dofs(igasf_handle h) { return h ? h->Ntot : -1; }
 
-int64_t igasf_num_quad_points(igasf_handle h) { return h ? h->Qtot : -1; }
+int64_t igasf_num_quad_points(igasf_handle h) { return h ? h->Qapi : -1; }
 
 int igasf_describe(igasf_handle h, int prec, igasf_plan_desc *out) {
   if (!h || !out) return fail(IGASF_ERR_INVALID_ARG, "handle or out is NULL");
@@ -674,7 +725,7 @@ int igasf_describe(igasf_handle h, int prec, igasf_plan_desc *out) {
   out->threads_per_block = v.k.threads;
   out->kernel_variant = v.k.variant;
   out->num_dofs = h->Ntot;
-  out->num_quad_points = h->Qtot;
+  out->num_quad_points = h->Qapi;
   out->factor_bytes[IGASF_MASS] = (int64_t)v.bytesM;
   out->factor_bytes[IGASF_STIFFNESS] = (int64_t)v.bytesK;
   out->workspace_bytes = (int64_t)v.vpart_bytes;
@@ -687,20 +738,25 @@ int igasf_get_tables(igasf_handle h, int dir, double *nodes, double *weights, do
                      double *dB) {
   if (!h) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL");
   if (dir < 0 || dir >= h->d) return fail(IGASF_ERR_INVALID_ARG, "dir = %d", dir);
-  const int Q = h->Q[dir], p = h->p;
+  // output: the non-empty spans' points, i.e. full point elem[i] p + g for API point i p + g
+  const int Q = h->Q[dir], p = h->p, Qe = h->Ke[dir] * p;
+  auto full_q = [&](int q) { return h->elem[dir][q / p] * p + q % p; };
   cudaError_t e = cudaSuccess;
-  if (nodes) e = cudaMemcpy(nodes, h->nodes[dir], sizeof(double) * Q, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && weights)
-    e = cudaMemcpy(weights, h->weights[dir], sizeof(double) * Q, cudaMemcpyDeviceToHost);
-  std::vector<double> tmp;
-  if (e == cudaSuccess && (B || dB)) tmp.resize((size_t)Q * p);
+  std::vector<double> tmp((size_t)Q * p);
+  for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+    double *dst = which ? weights : nodes;
+    if (!dst) continue;
+    e = cudaMemcpy(tmp.data(), which ? h->weights[dir] : h->nodes[dir], sizeof(double) * Q,
+                   cudaMemcpyDeviceToHost);
+    for (int q = 0; q < Qe && e == cudaSuccess; ++q) dst[q] = tmp[full_q(q)];
+  }
   for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
     double *dst = which ? dB : B;
     if (!dst) continue;
     e = cudaMemcpy(tmp.data(), which ? h->tabD[dir] : h->tabB[dir], sizeof(double) * Q * p,
                    cudaMemcpyDeviceToHost);
-    for (int q = 0; q < Q && e == cudaSuccess; ++q)
-      for (int j = 0; j < p; ++j) dst[(size_t)q * p + j] = tmp[(size_t)j * Q + q];
+    for (int q = 0; q < Qe && e == cudaSuccess; ++q)
+      for (int j = 0; j < p; ++j) dst[(size_t)q * p + j] = tmp[(size_t)j * Q + full_q(q)];
   }
   if (e != cudaSuccess) return cuda_fail(e, "copy tables");
   return IGASF_OK;
@@ -734,7 +790,15 @@ int igasf_quad_points(igasf_handle h, double *xyz_host) {
     g.xq_out = tmp;
     e = launch_geometry(g, nullptr);
   }
-  if (e == cudaSuccess) e = cudaMemcpy(xyz_host, tmp, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    if (h->empty_spans) {
+      std::vector<double> full((size_t)h->Qtot * h->d);
+      e = cudaMemcpy(full.data(), tmp, bytes, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) compact_qp(h, full.data(), xyz_host, h->d);
+    } else {
+      e = cudaMemcpy(xyz_host, tmp, bytes, cudaMemcpyDeviceToHost);
+    }
+  }
   cudaFree(tmp);
   cudaFree(bad);
   if (e != cudaSuccess) return cuda_fail(e, "quadrature points");
@@ -754,7 +818,15 @@ int igasf_get_factors(igasf_handle h, int op, int prec, double *out) {
   cudaError_t e = cudaMalloc((void **)&tmp, bytes);
   if (e != cudaSuccess) return cuda_fail(e, "export buffer");
   e = launch_export_factors(h->var[prec].L, op, h->Qtot, h->Q, tmp, nullptr);
-  if (e == cudaSuccess) e = cudaMemcpy(out, tmp, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    if (h->empty_spans) {
+      std::vector<double> full((size_t)h->Qtot * nf);
+      e = cudaMemcpy(full.data(), tmp, bytes, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) compact_qp(h, full.data(), out, nf);
+    } else {
+      e = cudaMemcpy(out, tmp, bytes, cudaMemcpyDeviceToHost);
+    }
+  }
   cudaFree(tmp);
   if (e != cudaSuccess) return cuda_fail(e, "export factors");
   return IGASF_OK;

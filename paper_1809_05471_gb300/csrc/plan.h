@@ -35,8 +35,20 @@ struct Variant {
 
 struct igasf_plan {
   int d = 0, p = 0, device = 0;
+  // Elements are all knot spans [t_k, t_k+1), k = p-1 .. nk-p-1, empty ones
+  // included, so that the first function of element e is e in every
+  // direction; an empty span has zero weights, tables and factors and adds
+  // nothing. K, Q and Qtot count these elements; the API's quadrature points
+  // (num_quad_points, tables, factors, points, per-point coefficients) are
+  // those of the non-empty spans only: Ke per direction, Qapi in all, with
+  // elem[a][i] the element of the i-th non-empty span.
   int N[igasf::kMaxDim] = {1, 1, 1}, K[igasf::kMaxDim] = {1, 1, 1}, Q[igasf::kMaxDim] = {1, 1, 1};
   int64_t Ntot = 0, Qtot = 0;
+  int Ke[igasf::kMaxDim] = {1, 1, 1};
+  int64_t Qapi = 0;
+  bool empty_spans = false;
+  std::vector<int> elem[igasf::kMaxDim];
+  std::vector<unsigned char> nonempty[igasf::kMaxDim];   // per element: 1 if its span is non-empty
   double *knots[igasf::kMaxDim] = {nullptr, nullptr, nullptr};
   int *span[igasf::kMaxDim] = {nullptr, nullptr, nullptr};
   double *nodes[igasf::kMaxDim] = {nullptr, nullptr, nullptr};

@@ -19,7 +19,9 @@ namespace igasf {
 // method on the Legendre polynomial of degree p), its weight, and the p
 // non-zero B-splines there with their derivatives, by de Boor's triangular
 // scheme (values of orders 1..p on the span, derivative from the order p-1
-// values). Output layout [j][Q]: entry j is function (first active) + j.
+// values). Output layout [j][Q]: entry j is function (first active) + j. An
+// empty span (a repeated knot) is an element of zero measure: its points sit
+// at the knot with weight 0, and its table entries are 0.
 // ---------------------------------------------------------------------------
 __global__ void tables_kernel(int p, int K, const double *__restrict__ knots,
                               const int *__restrict__ span, double *nodes, double *weights,
@@ -60,6 +62,13 @@ __global__ void tables_kernel(int p, int K, const double *__restrict__ knots,
   const double x = lo + 0.5 * (z + 1.0) * (hi - lo);
   nodes[q] = x;
   weights[q] = 0.5 * wg * (hi - lo);
+  if (!(hi > lo)) {
+    for (int s = 0; s < p; ++s) {
+      tabB[s * Q + q] = 0.0;
+      tabD[s * Q + q] = 0.0;
+    }
+    return;
+  }
 
   double Nv[IGASF_MAX_ORDER], Nm1[IGASF_MAX_ORDER], left[IGASF_MAX_ORDER], right[IGASF_MAX_ORDER];
   Nv[0] = 1.0;
@@ -248,9 +257,9 @@ __global__ void geometry3d_kernel(const GeometryParams g, int Gs, int nb1, int n
       adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
       adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
       const double det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
-      if (!(det > 0.0)) atomicOr(g.bad_det, 1u);
-      const double adet = fabs(det);
       const double w = g.wq[0][q1g] * g.wq[1][q2g] * g.wq[2][q3g];
+      if (w > 0.0 && !(det > 0.0)) atomicOr(g.bad_det, 1u);   // w = 0: an empty span
+      const double adet = fabs(det);
       const int64_t qlin = ((int64_t)q3g * Qt2 + q2g) * Qt1 + q1g;
       const double a = coefficient(g, X, qlin);
       const double s = adet > 0.0 ? w * a / adet : 0.0;
@@ -276,7 +285,7 @@ __global__ void geometry2d_kernel(const GeometryParams g) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)Qt1 * Qt2) return;
   const int q1g = (int)(q % Qt1), q2g = (int)(q / Qt1);
-  const int f1 = q1g / P, f2 = q2g / P;  // first active function = element (simple knots)
+  const int f1 = q1g / P, f2 = q2g / P;  // first active function = element (span index - p + 1)
   double X[2] = {0.0, 0.0}, J[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
   for (int j2 = 0; j2 < P; ++j2) {
     const double b2 = g.tabB[1][j2 * Qt2 + q2g], d2 = g.tabD[1][j2 * Qt2 + q2g];
@@ -292,11 +301,11 @@ __global__ void geometry2d_kernel(const GeometryParams g) {
     }
   }
   const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-  if (!(det > 0.0)) atomicOr(g.bad_det, 1u);
+  const double w = g.wq[0][q1g] * g.wq[1][q2g];
+  if (w > 0.0 && !(det > 0.0)) atomicOr(g.bad_det, 1u);   // w = 0: an empty span
   const double adet = fabs(det);
   // adj = det J^-1 = [[J11, -J01], [-J10, J00]]
   const double adj[2][2] = {{J[1][1], -J[0][1]}, {-J[1][0], J[0][0]}};
-  const double w = g.wq[0][q1g] * g.wq[1][q2g];
   const double a = coefficient(g, X, q);
   const double s = adet > 0.0 ? w * a / adet : 0.0;
   double dk[3];

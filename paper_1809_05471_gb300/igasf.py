@@ -266,8 +266,8 @@ class Plan:
         """(nodes, weights, B[Q, p], dB[Q, p]) of one direction, FP64 from the device."""
         desc = self.describe(self.precisions[0])
         p = desc["order"]
-        # Q of this direction from the knot vector: simple knots, K = nk - 2p + 1
-        Q = (len(self._knots[direction]) - 2 * p + 1) * p
+        # Q of this direction from the knot vector: p points per non-empty span
+        Q = int(np.count_nonzero(np.diff(np.asarray(self._knots[direction])) > 0)) * p
         nodes, weights = np.zeros(Q), np.zeros(Q)
         B, dB = np.zeros((Q, p)), np.zeros((Q, p))
         _check(load_library().igasf_get_tables(self._h(), direction, _dptr(nodes), _dptr(weights),

@@ -239,6 +239,30 @@ def test_dense_matches_brute_force_repeated_knots():
         assert np.max(np.abs(A - Ab)) < 1e-13 * np.max(np.abs(Ab))
 
 
+@pytest.mark.parametrize("bits", [0, O.BF16_BITS])
+def test_point_and_row_apply_match_brute_force_repeated_knots(bits):
+    # the two matrix-free oracle applies on empty spans: nothing of a repeated
+    # knot's zero-length span may enter, with exact or bfloat16-rounded factors
+    p = 4
+    knots = [I.open_knots_from_breaks(p, [0, 0.3, 0.6, 1.0], [2, 3]),
+             I.open_knots_from_breaks(p, [0, 0.5, 1.0], [1]),
+             I.open_knots_from_breaks(p, [0, 0.25, 1.0], [2])]
+    patch, u = I.make_patch(3, p, [3, 2, 2], noise_amp=0.01, seed=5, knots=knots,
+                            coef_kind=I.COEF_EXP_SIN_COS, coef_alpha=0.5)
+    rf = None if bits == 0 else (lambda x: np.ldexp(np.round(np.frexp(x)[0] * 256.0),
+                                                    np.frexp(x)[1] - 8))
+    rows = np.arange(patch.num_dofs)
+    for op in (O.MASS, O.STIFFNESS):
+        Ab = brute.dense_operator(patch, op, round_factor=rf)
+        with O.stored_factor_bits(bits):
+            vq = O.apply_qp(patch, op, u)
+            vr, ra = O.apply_rows(patch, op, u, rows)
+        s = np.max(np.abs(Ab)) * np.max(np.abs(u))
+        assert np.max(np.abs(vq - Ab @ u)) < 1e-13 * s
+        assert np.max(np.abs(vr - Ab @ u)) < 1e-13 * s
+        assert np.max(np.abs(ra - np.abs(Ab).sum(axis=1))) < 1e-13 * np.max(ra)
+
+
 # --- Kronecker identity for the identity geometry (Sec. 5) -------------------
 
 @pytest.mark.parametrize("p", [2, 3, 4])
