@@ -467,24 +467,26 @@ cudaError_t launch_apply3d_f32r_batched(const BatchParams &bp, int blocks, cudaS
   return cudaGetLastError();
 }
 
-template <int P, int S1, int S2, int S3, int PD, bool BF, int RL, int MINB>
-cudaError_t prepare_apply3d_f32r() {
+template <int P, int S1, int S2, int S3, bool STIFF, int PD, bool BF, int RL, int MINB>
+cudaError_t prepare_apply3d_f32r_op() {
   using G = TileF2R<P, S1, S2, S3>;
-  const int sm = (int)(G::smem_floats(false) * sizeof(float));
-  const int sk = (int)(G::smem_floats(true) * sizeof(float));
+  const int sh = (int)(G::smem_floats(STIFF) * sizeof(float));
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
   if constexpr (MINB > 0) {
-    e = cudaFuncSetAttribute(apply3d_f32r_kernel_mb<P, S1, S2, S3, false, PD, BF, RL, MINB>, a, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel_mb<P, S1, S2, S3, true, PD, BF, RL, MINB>, a, sk);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched_mb<P, S1, S2, S3, false, PD, BF, RL, MINB>, a, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched_mb<P, S1, S2, S3, true, PD, BF, RL, MINB>, a, sk);
+    e = cudaFuncSetAttribute(apply3d_f32r_kernel_mb<P, S1, S2, S3, STIFF, PD, BF, RL, MINB>, a, sh);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched_mb<P, S1, S2, S3, STIFF, PD, BF, RL, MINB>, a, sh);
   } else {
-    e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, false, PD, BF, RL>, a, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, true, PD, BF, RL>, a, sk);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF, RL>, a, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF, RL>, a, sk);
+    e = cudaFuncSetAttribute(apply3d_f32r_kernel<P, S1, S2, S3, STIFF, PD, BF, RL>, a, sh);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(apply3d_f32r_batched<P, S1, S2, S3, STIFF, PD, BF, RL>, a, sh);
   }
+  return e;
+}
+
+template <int P, int S1, int S2, int S3, int PD, bool BF, int RL, int MINB, int MINBM>
+cudaError_t prepare_apply3d_f32r() {
+  cudaError_t e = prepare_apply3d_f32r_op<P, S1, S2, S3, false, PD, BF, RL, MINBM>();
+  if (e == cudaSuccess) e = prepare_apply3d_f32r_op<P, S1, S2, S3, true, PD, BF, RL, MINB>();
   return e;
 }
 
@@ -492,9 +494,13 @@ cudaError_t prepare_apply3d_f32r() {
 // resident blocks per SM asked of the register allocator (0: its own choice).
 // RL: flags; kReloadTables: phase C reads the direction-3 tables again for the
 // transposed sweep instead of keeping them live across the product;
-// kL2Prefetch: the tile requests its factors into L2 at entry.
-template <int P, int S1, int S2, int S3, bool BF = false, int PD = 2, int MINB = 0, int RL = 0>
+// kL2Prefetch: the tile requests its factors into L2 at entry. MINBM: the
+// mass kernel's minimum resident blocks where it differs from MINB (0: the
+// same); the mass keeps fewer values per thread and fits more blocks.
+template <int P, int S1, int S2, int S3, bool BF = false, int PD = 2, int MINB = 0, int RL = 0,
+          int MINBM = 0>
 ApplyKernel make_apply3d_f32r() {
+  constexpr int MB_MASS = MINBM ? MINBM : MINB;
   using G = TileF2R<P, S1, S2, S3>;
   static_assert(G::NT <= 1024, "tile too large for one block");
   static_assert(G::smem_floats(true) * sizeof(float) <= 227 * 1024, "tile exceeds shared memory");
@@ -508,11 +514,11 @@ ApplyKernel make_apply3d_f32r() {
   k.plane = G::PL;
   k.lanes = 2;
   k.variant = IGASF_KERNEL_REGISTERS;
-  k.launch[IGASF_MASS] = &launch_apply3d_f32r<P, S1, S2, S3, false, PD, BF, RL, MINB>;
+  k.launch[IGASF_MASS] = &launch_apply3d_f32r<P, S1, S2, S3, false, PD, BF, RL, MB_MASS>;
   k.launch[IGASF_STIFFNESS] = &launch_apply3d_f32r<P, S1, S2, S3, true, PD, BF, RL, MINB>;
-  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF, RL, MINB>;
+  k.launch_batched[IGASF_MASS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, false, PD, BF, RL, MB_MASS>;
   k.launch_batched[IGASF_STIFFNESS] = &launch_apply3d_f32r_batched<P, S1, S2, S3, true, PD, BF, RL, MINB>;
-  k.prepare = &prepare_apply3d_f32r<P, S1, S2, S3, PD, BF, RL, MINB>;
+  k.prepare = &prepare_apply3d_f32r<P, S1, S2, S3, PD, BF, RL, MINB, MB_MASS>;
   return k;
 }
 

@@ -69,6 +69,11 @@ tc = {
 # (FP32 p = 3: 0.244 -> 0.215 ms; BF16 p = 4: 0.436 -> 0.385 ms; 2 to 7 % at
 # p = 7..9); off at the bench cube's p = 4 FP32, where it slowed the gather
 l2_prefetch = {"fp32": {3, 7, 8, 9}, "bf16": {4, 7, 8, 9}}
+# FP32 register-prefetch candidates whose mass kernel asks for more resident
+# blocks than the stiffness (order, tile): blocks; the 64^3, p = 4 cube's FP32
+# mass 31.0 -> 29.0 us with 6 (104 -> 80 registers, no spills; 7 and 8 blocks
+# measured the same as 6)
+mass_minb = {(4, "4, 4, 4"): 6}
 mk = {R: "make_apply3d_f32r", T: "make_apply3d_f32"}
 name = {R: "register prefetch", T: "TMA ring"}
 for P in range(2, 10):
@@ -78,9 +83,11 @@ for P in range(2, 10):
          "// BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:"]
     def describe(c):
         v, t = c[0], c[1]
-        return "%s, tile %s%s%s%s" % (name[v], t, (", registers capped for %d resident blocks" % c[2]) if len(c) > 2 and c[2] else "",
-                                     ", tables reloaded for the transposed sweep" if len(c) > 3 and c[3] else "",
-                                     " (BF16 too)" if len(c) > 4 and c[4] else "")
+        mbm = mass_minb.get((P, t), 0) if v == R else 0
+        return "%s, tile %s%s%s%s%s" % (name[v], t, (", registers capped for %d resident blocks" % c[2]) if len(c) > 2 and c[2] else "",
+                                       (" (mass %d, FP32)" % mbm) if mbm else "",
+                                       ", tables reloaded for the transposed sweep" if len(c) > 3 and c[3] else "",
+                                       " (BF16 too)" if len(c) > 4 and c[4] else "")
     for c in main[P]:
         if c[0] == "pair":
             L.append("//   FP32: %s; BF16: %s" % (describe(c[1]), describe(c[2])))
@@ -118,8 +125,10 @@ for P in range(2, 10):
                 # (measured faster for the bfloat16 stream at these orders)
                 mb16, f16 = 0, 0
             f16 |= 2 if P in l2_prefetch["bf16"] else 0
+            mbm = mass_minb.get((P, t), 0)
             return ("%s<%d, %s, true, 2, %d, %d>()" % (mk[v], P, t, mb16, f16),
-                    "%s<%d, %s, false, 2, %d, %d>()" % (mk[v], P, t, minb, f32))
+                    "%s<%d, %s, false, 2, %d, %d%s>()" % (mk[v], P, t, minb, f32,
+                                                           ", %d" % mbm if mbm else ""))
         if reload:
             return ("%s<%d, %s, true, true>()" % (mk[v], P, t), "%s<%d, %s, false, true>()" % (mk[v], P, t))
         return ("%s<%d, %s, true>()" % (mk[v], P, t), "%s<%d, %s>()" % (mk[v], P, t))
