@@ -15,6 +15,8 @@ autotuner; for odd p that shape has an odd number of direction-1 points per tile
 which the pencil-pair kernels cannot hold.
 
     python paper_1809_05471_gb300/csrc/gen_orders.py
+
+tests/test_generated_sources.py checks that the committed files are its output.
 """
 import os
 
@@ -76,83 +78,89 @@ l2_prefetch = {"fp32": {3, 7, 8, 9}, "bf16": {4, 7, 8, 9}}
 mass_minb = {(4, "4, 4, 4"): 6}
 mk = {R: "make_apply3d_f32r", T: "make_apply3d_f32"}
 name = {R: "register prefetch", T: "TMA ring"}
-for P in range(2, 10):
-    L = ["// 3D apply kernels of order p = %d. FP64: scalar kernel, tile %s elements." % (P, f64[P]),
-         "// FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep",
-         "// of tile shapes and factor-stream variants on the order-sweep workload);",
-         "// BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:"]
-    def describe(c):
-        v, t = c[0], c[1]
-        mbm = mass_minb.get((P, t), 0) if v == R else 0
-        return "%s, tile %s%s%s%s%s" % (name[v], t, (", registers capped for %d resident blocks" % c[2]) if len(c) > 2 and c[2] else "",
-                                       (" (mass %d, FP32)" % mbm) if mbm else "",
-                                       ", tables reloaded for the transposed sweep" if len(c) > 3 and c[3] else "",
-                                       " (BF16 too)" if len(c) > 4 and c[4] else "")
-    for c in main[P]:
-        if c[0] == "pair":
-            L.append("//   FP32: %s; BF16: %s" % (describe(c[1]), describe(c[2])))
-        else:
-            L.append("//   %s" % describe(c))
-    L.append("// Register-prefetch kernels request their tile's factors into L2 at entry: "
-             "FP32 %s, BF16 %s." % ("yes" if P in l2_prefetch["fp32"] else "no",
-                                   "yes" if P in l2_prefetch["bf16"] else "no"))
-    L.append("// IGASF_TILE_SEARCH compiles every listed shape in both variants.")
-    L.append("// Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): %s." % "; ".join(
-        "tile %s, %d warps" % (t, w) for t, w, _ in tc[P]))
-    L.append("// Factors evaluated on the fly (FP32): tile %s first, then %s." % (geo[P][0][0], geo[P][1][0]))
-    L.append('#include "apply3d.cuh"\n#include "apply3d_f32.cuh"\n#include "apply3d_f32g.cuh"\n#include "apply3d_f32r.cuh"\n#include "apply3d_tc.cuh"\n\nnamespace igasf {\n')
-    L.append("int apply3d_p%d(int prec, ApplyKernel *out, int max_out) {" % P)
-    L.append("  int n = 0;\n  if (prec == IGASF_FP64) {")
-    L.append("    if (n < max_out) out[n++] = make_apply3d<double, %d, %s>();\n    return n;\n  }" % (P, f64[P]))
-    L.append("  if (tensor_core_prec(prec)) {\n    const bool b = prec == IGASF_BF16_MMA;")
-    for t, w, mb in tc[P]:
-        L.append("    if (n < max_out) out[n++] = b ? make_apply3d_tc<%d, %s, TC_BF16, %d, %d>() : make_apply3d_tc<%d, %s, TC_TF32, %d, %d>();"
-                 % (P, t, w, mb, P, t, w, mb))
-    L.append("    return n;\n  }")
-    L.append("  const bool bf = prec == IGASF_BF16;")
-    L.append("#ifndef IGASF_TILE_SEARCH")
-    def inst(c):
-        """(BF16, FP32) instantiations of a candidate (variant, tile[, minb[, reload[, BF16 too]]])."""
-        v, t = c[0], c[1]
-        minb = c[2] if len(c) > 2 else 0
-        reload = bool(len(c) > 3 and c[3])
-        if v == R:
-            f32 = (1 if reload else 0) | (2 if P in l2_prefetch["fp32"] else 0)
-            if len(c) > 4 and c[4]:
-                mb16, f16 = minb, (1 if reload else 0)
+def generate(outdir=HERE):
+    """Write apply3d_p{2..9}.cu into outdir."""
+    for P in range(2, 10):
+        L = ["// 3D apply kernels of order p = %d. FP64: scalar kernel, tile %s elements." % (P, f64[P]),
+             "// FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep",
+             "// of tile shapes and factor-stream variants on the order-sweep workload);",
+             "// BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:"]
+        def describe(c):
+            v, t = c[0], c[1]
+            mbm = mass_minb.get((P, t), 0) if v == R else 0
+            return "%s, tile %s%s%s%s%s" % (name[v], t, (", registers capped for %d resident blocks" % c[2]) if len(c) > 2 and c[2] else "",
+                                           (" (mass %d, FP32)" % mbm) if mbm else "",
+                                           ", tables reloaded for the transposed sweep" if len(c) > 3 and c[3] else "",
+                                           " (BF16 too)" if len(c) > 4 and c[4] else "")
+        for c in main[P]:
+            if c[0] == "pair":
+                L.append("//   FP32: %s; BF16: %s" % (describe(c[1]), describe(c[2])))
             else:
-                # BF16 keeps the compiler's register choice and the tables in registers
-                # (measured faster for the bfloat16 stream at these orders)
-                mb16, f16 = 0, 0
-            f16 |= 2 if P in l2_prefetch["bf16"] else 0
-            mbm = mass_minb.get((P, t), 0)
-            return ("%s<%d, %s, true, 2, %d, %d>()" % (mk[v], P, t, mb16, f16),
-                    "%s<%d, %s, false, 2, %d, %d%s>()" % (mk[v], P, t, minb, f32,
-                                                           ", %d" % mbm if mbm else ""))
-        if reload:
-            return ("%s<%d, %s, true, true>()" % (mk[v], P, t), "%s<%d, %s, false, true>()" % (mk[v], P, t))
-        return ("%s<%d, %s, true>()" % (mk[v], P, t), "%s<%d, %s>()" % (mk[v], P, t))
-    def inst2(c):
-        """("pair", FP32 candidate, BF16 candidate): different defaults per precision."""
-        if c[0] == "pair":
-            return inst(c[2])[0], inst(c[1])[1]
-        return inst(c)
-    for c in main[P]:
-        b16, f32 = inst2(c)
+                L.append("//   %s" % describe(c))
+        L.append("// Register-prefetch kernels request their tile's factors into L2 at entry: "
+                 "FP32 %s, BF16 %s." % ("yes" if P in l2_prefetch["fp32"] else "no",
+                                       "yes" if P in l2_prefetch["bf16"] else "no"))
+        L.append("// IGASF_TILE_SEARCH compiles every listed shape in both variants.")
+        L.append("// Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): %s." % "; ".join(
+            "tile %s, %d warps" % (t, w) for t, w, _ in tc[P]))
+        L.append("// Factors evaluated on the fly (FP32): tile %s first, then %s." % (geo[P][0][0], geo[P][1][0]))
+        L.append('#include "apply3d.cuh"\n#include "apply3d_f32.cuh"\n#include "apply3d_f32g.cuh"\n#include "apply3d_f32r.cuh"\n#include "apply3d_tc.cuh"\n\nnamespace igasf {\n')
+        L.append("int apply3d_p%d(int prec, ApplyKernel *out, int max_out) {" % P)
+        L.append("  int n = 0;\n  if (prec == IGASF_FP64) {")
+        L.append("    if (n < max_out) out[n++] = make_apply3d<double, %d, %s>();\n    return n;\n  }" % (P, f64[P]))
+        L.append("  if (tensor_core_prec(prec)) {\n    const bool b = prec == IGASF_BF16_MMA;")
+        for t, w, mb in tc[P]:
+            L.append("    if (n < max_out) out[n++] = b ? make_apply3d_tc<%d, %s, TC_BF16, %d, %d>() : make_apply3d_tc<%d, %s, TC_TF32, %d, %d>();"
+                     % (P, t, w, mb, P, t, w, mb))
+        L.append("    return n;\n  }")
+        L.append("  const bool bf = prec == IGASF_BF16;")
+        L.append("#ifndef IGASF_TILE_SEARCH")
+        def inst(c):
+            """(BF16, FP32) instantiations of a candidate (variant, tile[, minb[, reload[, BF16 too]]])."""
+            v, t = c[0], c[1]
+            minb = c[2] if len(c) > 2 else 0
+            reload = bool(len(c) > 3 and c[3])
+            if v == R:
+                f32 = (1 if reload else 0) | (2 if P in l2_prefetch["fp32"] else 0)
+                if len(c) > 4 and c[4]:
+                    mb16, f16 = minb, (1 if reload else 0)
+                else:
+                    # BF16 keeps the compiler's register choice and the tables in registers
+                    # (measured faster for the bfloat16 stream at these orders)
+                    mb16, f16 = 0, 0
+                f16 |= 2 if P in l2_prefetch["bf16"] else 0
+                mbm = mass_minb.get((P, t), 0)
+                return ("%s<%d, %s, true, 2, %d, %d>()" % (mk[v], P, t, mb16, f16),
+                        "%s<%d, %s, false, 2, %d, %d%s>()" % (mk[v], P, t, minb, f32,
+                                                               ", %d" % mbm if mbm else ""))
+            if reload:
+                return ("%s<%d, %s, true, true>()" % (mk[v], P, t), "%s<%d, %s, false, true>()" % (mk[v], P, t))
+            return ("%s<%d, %s, true>()" % (mk[v], P, t), "%s<%d, %s>()" % (mk[v], P, t))
+        def inst2(c):
+            """("pair", FP32 candidate, BF16 candidate): different defaults per precision."""
+            if c[0] == "pair":
+                return inst(c[2])[0], inst(c[1])[1]
+            return inst(c)
+        for c in main[P]:
+            b16, f32 = inst2(c)
+            L.append("  if (n < max_out) out[n++] = bf ? %s : %s;" % (b16, f32))
+        L.append("#else")
+        first = main[P][0]
+        b16, f32 = inst2(first)
         L.append("  if (n < max_out) out[n++] = bf ? %s : %s;" % (b16, f32))
-    L.append("#else")
-    first = main[P][0]
-    b16, f32 = inst2(first)
-    L.append("  if (n < max_out) out[n++] = bf ? %s : %s;" % (b16, f32))
-    firsts = [first[1][:2], first[2][:2]] if first[0] == "pair" else [tuple(first[:2])]
-    for v in (R, T):
-        for t in search[P]:
-            if (v, t) in [tuple(f) for f in firsts]:
-                continue
-            L.append("  if (n < max_out) out[n++] = bf ? %s<%d, %s, true>() : %s<%d, %s>();" % (mk[v], P, t, mk[v], P, t))
-    L.append("#endif\n  return n;\n}\n")
-    L.append("int apply3d_p%d_geo(ApplyKernel *out, int max_out) {\n  int n = 0;" % P)
-    for t, z in geo[P]:
-        L.append("  if (n < max_out) out[n++] = make_apply3d_f32g<%d, %s, %s>();" % (P, t, "true" if z else "false"))
-    L.append("  return n;\n}\n\n}  // namespace igasf")
-    open(os.path.join(HERE, "apply3d_p%d.cu" % P), "w").write("\n".join(L) + "\n")
+        firsts = [first[1][:2], first[2][:2]] if first[0] == "pair" else [tuple(first[:2])]
+        for v in (R, T):
+            for t in search[P]:
+                if (v, t) in [tuple(f) for f in firsts]:
+                    continue
+                L.append("  if (n < max_out) out[n++] = bf ? %s<%d, %s, true>() : %s<%d, %s>();" % (mk[v], P, t, mk[v], P, t))
+        L.append("#endif\n  return n;\n}\n")
+        L.append("int apply3d_p%d_geo(ApplyKernel *out, int max_out) {\n  int n = 0;" % P)
+        for t, z in geo[P]:
+            L.append("  if (n < max_out) out[n++] = make_apply3d_f32g<%d, %s, %s>();" % (P, t, "true" if z else "false"))
+        L.append("  return n;\n}\n\n}  // namespace igasf")
+        open(os.path.join(outdir, "apply3d_p%d.cu" % P), "w").write("\n".join(L) + "\n")
+
+
+if __name__ == "__main__":
+    generate()
