@@ -193,7 +193,9 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
  * localized per Sec. 4). u and v: device arrays of num_dofs values of the
  * precision's type (double for FP64, float for FP32 and BF16), aligned to it,
  * not overlapping. v is overwritten. Asynchronous: returns after enqueueing; it
- * allocates nothing and does not synchronise. Errors: INVALID_ARG (null or
+ * allocates nothing and does not synchronise, so it may be captured into a CUDA
+ * graph (two kernel nodes: the tile kernel, then the gather with a programmatic
+ * dependency). Errors: INVALID_ARG (null or
  * misaligned pointer, bad op), UNSUPPORTED (precision not stored at setup),
  * CUDA (launch failure).
  */

@@ -265,6 +265,42 @@ def test_tiny_patches_single_partial_tile(d, p, K):
                 assert scaled_err(gpu_apply(plan, op, u, prec), v_ref, a_inf, u) < tol(prec, patch)
 
 
+def test_apply_is_cuda_graph_capturable():
+    """igasf_apply allocates nothing and never synchronizes with the host, so a
+    caller can capture it (tile kernel, then the gather with its programmatic
+    launch) into a CUDA graph: replays equal direct applies bit for bit, also
+    after the input buffer's values change."""
+    import torch
+    patch, u = I.make_patch(3, 4, [9, 6, 5], noise_amp=0.02, seed=5,
+                            coef_kind=I.COEF_EXP_SIN_COS, coef_alpha=0.5)
+    precs = (G.FP64, G.FP32, G.BF16, G.TF32, G.BF16_MMA)
+    with G.Plan.from_patch(patch, precisions=precs) as plan:
+        for prec in precs:
+            dt = torch.float64 if prec == G.FP64 else torch.float32
+            for op in (G.MASS, G.STIFFNESS):
+                ud = torch.as_tensor(u, device="cuda").to(dt)
+                v = torch.full_like(ud, float("nan"))
+                s = torch.cuda.Stream()
+                s.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(s):
+                    plan.apply(op, ud, v, prec=prec)      # warm-up outside the capture
+                torch.cuda.current_stream().wait_stream(s)
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s):
+                    plan.apply(op, ud, v, prec=prec)
+                for scale in (1.0, -0.5):
+                    ud.mul_(scale)
+                    v_ref = torch.empty_like(ud)
+                    plan.apply(op, ud, v_ref, prec=prec)
+                    v.fill_(float("nan"))
+                    g.replay()
+                    torch.cuda.synchronize()
+                    assert torch.equal(v, v_ref), (prec, op, scale)
+                assert plan.device_status() == 0
+                del g
+
+
 def test_apply_is_deterministic_and_host_path_matches():
     import torch
     patch, u = I.config_cube(p=3, K=20)
