@@ -217,11 +217,15 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
   }
   __syncthreads();
 
-  // ---- C: pencil pairs: direction-3 sweep, product with D, transposed sweep
+  // ---- C: pencil pairs: direction-3 sweep, product with D, transposed sweep.
+  // Element e3 reads y[e3 .. e3 + P - 1] and adds to z[e3 .. e3 + P - 1], so
+  // y[n] is read from shared memory when element n - P + 1 first needs it and
+  // z[n] written back as soon as element n has added to it: P live values per
+  // array instead of E3 (the same arithmetic in the same order).
   if (has_pair) {
     float2 y0[E3], y1[E3], y2[E3], z0[E3], z1[E3], z2[E3];
 #pragma unroll
-    for (int n = 0; n < E3; ++n) {
+    for (int n = 0; n < P - 1; ++n) {
       y0[n] = Y0[n * NPAIR + tid];
       z0[n] = make_float2(0.f, 0.f);
       if (STIFF) {
@@ -233,6 +237,17 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
     }
 #pragma unroll
     for (int e3 = 0; e3 < S3; ++e3) {
+      {
+        const int n = e3 + P - 1;
+        y0[n] = Y0[n * NPAIR + tid];
+        z0[n] = make_float2(0.f, 0.f);
+        if (STIFF) {
+          y1[n] = Y1[n * NPAIR + tid];
+          y2[n] = Y2[n * NPAIR + tid];
+          z1[n] = z0[n];
+          z2[n] = z0[n];
+        }
+      }
       if (e3 < ke3) {
 #pragma unroll
         for (int qq = 0; qq < P; ++qq) {
@@ -319,9 +334,14 @@ __device__ __forceinline__ void apply3d_f32r_body(const ApplyParams &prm, const 
           }
         }
       }
+      Y0[e3 * NPAIR + tid] = z0[e3];   // complete: no later element adds to z[e3]
+      if (STIFF) {
+        Y1[e3 * NPAIR + tid] = z1[e3];
+        Y2[e3 * NPAIR + tid] = z2[e3];
+      }
     }
 #pragma unroll
-    for (int n = 0; n < E3; ++n) {
+    for (int n = S3; n < E3; ++n) {
       Y0[n * NPAIR + tid] = z0[n];
       if (STIFF) {
         Y1[n * NPAIR + tid] = z1[n];
