@@ -29,7 +29,7 @@ main = {
  4: [(R, "4, 4, 4", 4, 1), (T, "8, 4, 2"), (T, "4, 4, 4"), (R, "4, 4, 1")],
  5: [(T, "4, 4, 4"), (R, "4, 4, 4"), (R, "4, 2, 4")],
  6: [(R, "2, 2, 8", 4, 1, 1), (R, "2, 2, 2", 4), (R, "4, 4, 2"), (T, "4, 2, 2")],
- 7: [("pair", (R, "2, 2, 6", 2, 1), (R, "2, 2, 8")), ("pair", (R, "2, 2, 8", 3, 1), (R, "2, 2, 6")),
+ 7: [("pair", (R, "2, 2, 6", 3, 1), (R, "2, 2, 8")), ("pair", (R, "2, 2, 8", 3, 1), (R, "2, 2, 6")),
      (T, "2, 2, 4", 0, 1), (R, "4, 2, 2")],
  8: [(R, "2, 2, 8"), (R, "2, 2, 6"), (R, "2, 2, 2"), (T, "4, 2, 1")],
  9: [(R, "2, 2, 6", 2, 1, 1), (R, "2, 2, 8", 2, 1), (R, "2, 2, 2", 2, 1), (T, "2, 2, 2")],
@@ -76,6 +76,10 @@ l2_prefetch = {"fp32": {3, 7, 8, 9}, "bf16": {4, 7, 8, 9}}
 # mass 31.0 -> 29.0 us with 6 (104 -> 80 registers, no spills; 7 and 8 blocks
 # measured the same as 6)
 mass_minb = {(4, "4, 4, 4"): 6}
+# Caps re-measured after phase C kept only p live values per array: p = 7 FP32
+# 3 blocks instead of 2 (168 registers, 4 bytes spilled; 2M dofs 3.61 -> 3.36 ms);
+# BF16 p = 6 at 5 blocks and p = 7 at 3 blocks (with reload) were slower (1.78 ->
+# 1.94, 2.72 -> 2.91 ms), p = 8 spills at any cap, p = 9 at 3 blocks spills 5 KB
 mk = {R: "make_apply3d_f32r", T: "make_apply3d_f32"}
 name = {R: "register prefetch", T: "TMA ring"}
 def generate(outdir=HERE):
