@@ -617,11 +617,15 @@ def run_igasf(args):
         dist.destroy_process_group()
 
 
+SWEEP_WINDOWS = 4   # timed windows per order-sweep line after the first
+
+
 def order_sweep(orders, G, I, O, torch, stream, roofline):
     """The order sweep: p = 2..9 at about 2M dofs (127 - p elements per
     direction, the same perturbed cube and coefficient), stiffness in every
     precision (FP64 up to p = 6: its factors alone are 30 to 60 GB beyond), one
-    plan per precision at a time; GDoF/s per apply, tile-kernel roofline and the
+    plan per precision at a time; GDoF/s per apply (median of SWEEP_WINDOWS timed
+    windows, with the SM clocks sampled meanwhile), tile-kernel roofline and the
     scaled error on sampled rows against the FP64 oracle (and, for the bfloat16
     precisions, against the oracle's operator with the same rounded factors)."""
     import numpy as np
@@ -641,17 +645,23 @@ def order_sweep(orders, G, I, O, torch, stream, roofline):
             ud = torch.as_tensor(u, device="cuda").to(torch.float64 if prec == "fp64" else torch.float32)
             ms, _, k_ms, _, _, _ = time_apply(plan, G.STIFFNESS, pc[prec], ud, 3, 2, stream)
             steps = steps_for(ms / 3)
-            ms, _, k_ms, g_ms, vd, _ = time_apply(plan, G.STIFFNESS, pc[prec], ud, steps, 3, stream)
+            # the first window, then SWEEP_WINDOWS more: the line reports their median
+            # (one window of 30 to 70 steps can catch a passing clock dip)
+            ms, rep, k_ms, g_ms, vd, ck = time_apply(plan, G.STIFFNESS, pc[prec], ud, steps, 3, stream,
+                                                     repeats=SWEEP_WINDOWS, clocks=True)
+            ms_step = rep["median_ms_per_step"]
             vs[prec] = vd.double().cpu().numpy()
             ok = ok and plan.device_status() == 0
             N, Q = plan.num_dofs, plan.num_quad_points
             lines.append({"workload": "order sweep", "p": p, "elements_per_dir": K, "dofs": N,
                           "quad_points": Q, "op": "stiffness", "prec": prec,
                           "tile": plan.describe(pc[prec])["tile"],
-                          "value": round(N / (ms / steps * 1e-3) / 1e9, 4),
-                          "ms_per_step": round(ms / steps, 5), "steps": steps,
+                          "value": round(N / (ms_step * 1e-3) / 1e9, 4),
+                          "ms_per_step": ms_step, "steps": steps,
+                          "windows": {"count": SWEEP_WINDOWS, "first_window_ms_per_step": round(ms / steps, 5),
+                                      "min": rep["min"], "max": rep["max"]},
                           "roofline": roofline("stiffness", prec, k_ms, Q, N, p, K, cube=False),
-                          "gather_ms": round(g_ms, 5), "setup_s": round(setup_s, 3)})
+                          "gather_ms": round(g_ms, 5), "setup_s": round(setup_s, 3), "clocks": ck})
             plan.close()
             del ud, vd
             torch.cuda.empty_cache()
