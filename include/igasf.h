@@ -444,10 +444,10 @@ int igasf_autotune(int d, const int *orders, const int *knot_lengths, const doub
 int igasf_list_kernels(int d, int p, int prec, int geometry, int *tiles, int *variants, int max_out);
 
 /*
- * Number of stored entries of the assembled matrix: the pairs (m, n) with
- * |m_a - n_a| <= p - 1 in every direction, which for simple interior knots is
- * prod_a ((2p - 1) K_a + (p - 1)^2) (Sec. 3.2, Corollary on nnz of B-spline
- * matrices). Returns a negative status on error.
+ * Number of stored entries of the assembled matrix: the pairs (m, n) whose
+ * functions share a non-empty element in every direction, which for simple
+ * interior knots is prod_a ((2p - 1) K_a + (p - 1)^2) (Sec. 3.2, Corollary on
+ * nnz of B-spline matrices). Returns a negative status on error.
  */
 int64_t igasf_assembled_nnz(igasf_handle h);
 

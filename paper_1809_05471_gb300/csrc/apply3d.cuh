@@ -3,7 +3,8 @@
 // with the factors, then Alg. 2; localized per Sec. 4, eq. loc-basis-change).
 //
 // Tile = S1 x S2 x S3 elements; its dofs are the (S+p-1)^3 functions active on
-// it (simple knots: element e carries functions e..e+p-1), its quadrature
+// it (element e carries functions e..e+p-1: every knot span is an element, the
+// empty spans of repeated knots included with zero weight), its quadrature
 // points the (S p)^3 Gauss points. One thread owns one "pencil": a fixed
 // (q1, q2) quadrature index in the tile, along all q3.
 //

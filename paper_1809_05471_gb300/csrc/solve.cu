@@ -69,7 +69,8 @@ __global__ void diag_kernel(const DiagParams g) {
   const int p = g.p;
   const int fi[6] = {0, 0, 0, 1, 1, 2}, fj[6] = {0, 1, 2, 1, 2, 2};
   double diag = 0.0;
-  // elements e with m - p + 1 <= e <= m (simple knots), inside the patch
+  // elements e with m - p + 1 <= e <= m, inside the patch (every knot span is an
+  // element; the empty spans of repeated knots have zero factors)
   for (int e2 = max(0, m[2] - p + 1); e2 <= min(g.K[2] - 1, m[2]); ++e2)
     for (int e1 = max(0, m[1] - p + 1); e1 <= min(g.K[1] - 1, m[1]); ++e1)
       for (int e0 = max(0, m[0] - p + 1); e0 <= min(g.K[0] - 1, m[0]); ++e0) {
