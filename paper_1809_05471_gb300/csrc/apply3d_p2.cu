@@ -2,8 +2,8 @@
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
 // BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
-//   register prefetch, tile 8, 8, 2
 //   register prefetch, tile 8, 8, 4
+//   register prefetch, tile 8, 8, 2
 //   TMA ring, tile 16, 8, 4
 //   register prefetch, tile 2, 2, 1
 // Register-prefetch kernels request their tile's factors into L2 at entry: FP32 no, BF16 no.
@@ -32,13 +32,13 @@ int apply3d_p2(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 2, true, 2, 0, 0>() : make_apply3d_f32r<2, 8, 8, 2, false, 2, 0, 0>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 4, true, 2, 0, 0>() : make_apply3d_f32r<2, 8, 8, 4, false, 2, 0, 0>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 2, true, 2, 0, 0>() : make_apply3d_f32r<2, 8, 8, 2, false, 2, 0, 0>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<2, 16, 8, 4, true>() : make_apply3d_f32<2, 16, 8, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 2, 2, 1, true, 2, 0, 0>() : make_apply3d_f32r<2, 2, 2, 1, false, 2, 0, 0>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 2, true, 2, 0, 0>() : make_apply3d_f32r<2, 8, 8, 2, false, 2, 0, 0>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 4, true>() : make_apply3d_f32r<2, 8, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 4, true, 2, 0, 0>() : make_apply3d_f32r<2, 8, 8, 4, false, 2, 0, 0>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 2, true>() : make_apply3d_f32r<2, 8, 8, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 16, 8, 4, true>() : make_apply3d_f32r<2, 16, 8, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 4, 8, true>() : make_apply3d_f32r<2, 8, 4, 8>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<2, 8, 8, 8, true>() : make_apply3d_f32r<2, 8, 8, 8>();

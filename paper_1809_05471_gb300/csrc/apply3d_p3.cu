@@ -2,8 +2,9 @@
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
 // BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
-//   FP32: register prefetch, tile 8, 4, 4, registers capped for 4 resident blocks, tables reloaded for the transposed sweep; BF16: TMA ring, tile 8, 8, 4
-//   FP32: TMA ring, tile 8, 8, 4; BF16: register prefetch, tile 8, 4, 4
+//   FP32: register prefetch, tile 8, 4, 4, registers capped for 4 resident blocks, tables reloaded for the transposed sweep; BF16: register prefetch, tile 4, 4, 8
+//   FP32: TMA ring, tile 8, 8, 4; BF16: TMA ring, tile 8, 8, 4
+//   FP32: register prefetch, tile 4, 4, 8; BF16: register prefetch, tile 8, 4, 4
 //   register prefetch, tile 4, 4, 4
 // Register-prefetch kernels request their tile's factors into L2 at entry: FP32 yes, BF16 no.
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
@@ -31,11 +32,12 @@ int apply3d_p3(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 4, 4, false, 2, 4, 3>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 4, 4, true, 2, 0, 0>() : make_apply3d_f32<3, 8, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 8, true, 2, 0, 0>() : make_apply3d_f32r<3, 8, 4, 4, false, 2, 4, 3>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32<3, 8, 8, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 4, 4, true, 2, 0, 0>() : make_apply3d_f32r<3, 4, 4, 8, false, 2, 0, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 4, true, 2, 0, 0>() : make_apply3d_f32r<3, 4, 4, 4, false, 2, 0, 2>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 4, 4, false, 2, 4, 3>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 8, true, 2, 0, 0>() : make_apply3d_f32r<3, 8, 4, 4, false, 2, 4, 3>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 4, 4, 4, true>() : make_apply3d_f32r<3, 4, 4, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 8, 4, true>() : make_apply3d_f32r<3, 8, 8, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 8, 2, true>() : make_apply3d_f32r<3, 8, 8, 2>();
@@ -43,6 +45,7 @@ int apply3d_p3(int prec, ApplyKernel *out, int max_out) {
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<3, 8, 4, 2, true>() : make_apply3d_f32r<3, 8, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 4, 4, true>() : make_apply3d_f32<3, 8, 4, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 4, 4, 4, true>() : make_apply3d_f32<3, 4, 4, 4>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 4, true>() : make_apply3d_f32<3, 8, 8, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 8, 2, true>() : make_apply3d_f32<3, 8, 8, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 4, 4, 2, true>() : make_apply3d_f32<3, 4, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<3, 8, 4, 2, true>() : make_apply3d_f32<3, 8, 4, 2>();

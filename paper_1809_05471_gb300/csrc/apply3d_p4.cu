@@ -2,7 +2,8 @@
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
 // BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
-//   register prefetch, tile 4, 4, 4, registers capped for 4 resident blocks (mass 6, FP32), tables reloaded for the transposed sweep
+//   FP32: register prefetch, tile 4, 4, 4, registers capped for 4 resident blocks (mass 6, FP32), tables reloaded for the transposed sweep; BF16: register prefetch, tile 4, 4, 8 (mass 6, FP32)
+//   FP32: register prefetch, tile 4, 4, 8, registers capped for 4 resident blocks (mass 6, FP32), tables reloaded for the transposed sweep; BF16: register prefetch, tile 4, 4, 4 (mass 6, FP32)
 //   TMA ring, tile 8, 4, 2
 //   TMA ring, tile 4, 4, 4
 //   register prefetch, tile 4, 4, 1
@@ -32,12 +33,13 @@ int apply3d_p4(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true, 2, 0, 2>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, 1, 6>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 8, true, 2, 0, 2>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, 1, 6>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true, 2, 0, 2>() : make_apply3d_f32r<4, 4, 4, 8, false, 2, 4, 1, 6>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 8, 4, 2, true>() : make_apply3d_f32<4, 8, 4, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<4, 4, 4, 4, true>() : make_apply3d_f32<4, 4, 4, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 1, true, 2, 0, 2>() : make_apply3d_f32r<4, 4, 4, 1, false, 2, 0, 0>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 4, true, 2, 0, 2>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, 1, 6>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 4, 8, true, 2, 0, 2>() : make_apply3d_f32r<4, 4, 4, 4, false, 2, 4, 1, 6>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 4, 2, 4, true>() : make_apply3d_f32r<4, 4, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 8, 4, 4, true>() : make_apply3d_f32r<4, 8, 4, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<4, 8, 4, 2, true>() : make_apply3d_f32r<4, 8, 4, 2>();

@@ -24,10 +24,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 R, T = "r", "t"
 f64 = {2: "8, 8, 8", 3: "8, 4, 4", 4: "4, 4, 4", 5: "4, 2, 2", 6: "4, 2, 2", 7: "2, 2, 2", 8: "2, 2, 2", 9: "2, 1, 2"}
 main = {
- 2: [(R, "8, 8, 2"), (R, "8, 8, 4"), (T, "16, 8, 4"), (R, "2, 2, 1")],
- 3: [("pair", (R, "8, 4, 4", 4, 1), (T, "8, 8, 4")), ("pair", (T, "8, 8, 4"), (R, "8, 4, 4")), (R, "4, 4, 4")],
- 4: [(R, "4, 4, 4", 4, 1), (T, "8, 4, 2"), (T, "4, 4, 4"), (R, "4, 4, 1")],
- 5: [(T, "4, 4, 4"), (R, "4, 4, 4"), (R, "4, 2, 4")],
+ 2: [(R, "8, 8, 4"), (R, "8, 8, 2"), (T, "16, 8, 4"), (R, "2, 2, 1")],
+ 3: [("pair", (R, "8, 4, 4", 4, 1), (R, "4, 4, 8")), ("pair", (T, "8, 8, 4"), (T, "8, 8, 4")),
+     ("pair", (R, "4, 4, 8"), (R, "8, 4, 4")), (R, "4, 4, 4")],
+ 4: [("pair", (R, "4, 4, 4", 4, 1), (R, "4, 4, 8")), ("pair", (R, "4, 4, 8", 4, 1), (R, "4, 4, 4")),
+     (T, "8, 4, 2"), (T, "4, 4, 4"), (R, "4, 4, 1")],
+ 5: [("pair", (T, "4, 4, 4"), (R, "4, 2, 8")), ("pair", (R, "4, 4, 4"), (T, "4, 4, 4")), (R, "4, 2, 4")],
  6: [(R, "2, 2, 8", 4, 1, 1), (R, "2, 2, 2", 4), (R, "4, 4, 2"), (T, "4, 2, 2")],
  7: [("pair", (R, "2, 2, 6", 3, 1), (R, "2, 2, 8")), ("pair", (R, "2, 2, 8", 3, 1), (R, "2, 2, 6")),
      (T, "2, 2, 4", 0, 1), (R, "4, 2, 2")],
@@ -75,8 +77,12 @@ l2_prefetch = {"fp32": {3, 7, 8, 9}, "bf16": {4, 7, 8, 9}}
 # blocks than the stiffness (order, tile): blocks; the 64^3, p = 4 cube's FP32
 # mass 31.0 -> 29.0 us with 6 (104 -> 80 registers, no spills; 7 and 8 blocks
 # measured the same as 6)
-mass_minb = {(4, "4, 4, 4"): 6}
-# Caps re-measured after phase C kept only p live values per array: p = 7 FP32
+mass_minb = {(4, "4, 4, 4"): 6, (4, "4, 4, 8"): 6}
+# Tiles re-measured after phase C kept only p live values per array (2M dofs,
+# stiffness, ms per apply): deeper tiles for BF16, p = 2 8x8x4 (0.084 -> 0.074;
+# FP32 0.091 -> 0.085 too), p = 3 4x4x8 (0.244 -> 0.211), p = 4 4x4x8 (0.405 ->
+# 0.372), p = 5 4x2x8 (1.134 -> 0.949); FP32 keeps its tiles at p = 3..5 (4x4x8 at
+# p = 4 spills at 4 blocks: 0.493 -> 0.575). Caps re-measured too: p = 7 FP32
 # 3 blocks instead of 2 (168 registers, 4 bytes spilled; 2M dofs 3.61 -> 3.36 ms);
 # BF16 p = 6 at 5 blocks and p = 7 at 3 blocks (with reload) were slower (1.78 ->
 # 1.94, 2.72 -> 2.91 ms), p = 8 spills at any cap, p = 9 at 3 blocks spills 5 KB
