@@ -3,8 +3,9 @@
 // of tile shapes and factor-stream variants on the order-sweep workload);
 // BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
 //   FP32: TMA ring, tile 4, 4, 4; BF16: register prefetch, tile 4, 2, 8
-//   FP32: register prefetch, tile 4, 4, 4; BF16: TMA ring, tile 4, 4, 4
+//   register prefetch, tile 4, 4, 4
 //   register prefetch, tile 4, 2, 4
+//   FP32: register prefetch, tile 4, 2, 8; BF16: TMA ring, tile 4, 4, 4
 // Register-prefetch kernels request their tile's factors into L2 at entry: FP32 no, BF16 no.
 // IGASF_TILE_SEARCH compiles every listed shape in both variants.
 // Tensor-core kernels (IGASF_TF32, IGASF_BF16_MMA): tile 4, 4, 4, 5 warps; tile 2, 2, 8, 7 warps.
@@ -32,8 +33,9 @@ int apply3d_p5(int prec, ApplyKernel *out, int max_out) {
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<5, 4, 2, 8, true, 2, 0, 0>() : make_apply3d_f32<5, 4, 4, 4>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32<5, 4, 4, 4, true>() : make_apply3d_f32r<5, 4, 4, 4, false, 2, 0, 0>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<5, 4, 4, 4, true, 2, 0, 0>() : make_apply3d_f32r<5, 4, 4, 4, false, 2, 0, 0>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<5, 4, 2, 4, true, 2, 0, 0>() : make_apply3d_f32r<5, 4, 2, 4, false, 2, 0, 0>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32<5, 4, 4, 4, true>() : make_apply3d_f32r<5, 4, 2, 8, false, 2, 0, 0>();
 #else
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<5, 4, 2, 8, true, 2, 0, 0>() : make_apply3d_f32<5, 4, 4, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<5, 4, 4, 4, true>() : make_apply3d_f32r<5, 4, 4, 4>();

@@ -29,7 +29,7 @@ main = {
      ("pair", (R, "4, 4, 8"), (R, "8, 4, 4")), (R, "4, 4, 4")],
  4: [("pair", (R, "4, 4, 4", 4, 1), (R, "4, 4, 8")), ("pair", (R, "4, 4, 8", 4, 1), (R, "4, 4, 4")),
      (T, "8, 4, 2"), (T, "4, 4, 4"), (R, "4, 4, 1")],
- 5: [("pair", (T, "4, 4, 4"), (R, "4, 2, 8")), ("pair", (R, "4, 4, 4"), (T, "4, 4, 4")), (R, "4, 2, 4")],
+ 5: [("pair", (T, "4, 4, 4"), (R, "4, 2, 8")), (R, "4, 4, 4"), (R, "4, 2, 4"), ("pair", (R, "4, 2, 8"), (T, "4, 4, 4"))],
  6: [(R, "2, 2, 8", 4, 1, 1), (R, "2, 2, 2", 4), (R, "4, 4, 2"), (T, "4, 2, 2")],
  7: [("pair", (R, "2, 2, 6", 3, 1), (R, "2, 2, 8")), ("pair", (R, "2, 2, 8", 3, 1), (R, "2, 2, 6")),
      (T, "2, 2, 4", 0, 1), (R, "4, 2, 2")],

@@ -18,3 +18,17 @@ def test_order_lists_are_the_generator_output(tmp_path):
         want = (tmp_path / name).read_text()
         with open(os.path.join(CSRC, name)) as f:
             assert f.read() == want, name + " differs from gen_orders.py's output"
+
+
+def test_persistent_batch_tiles_are_compiled_candidates():
+    # the persistent batch schedule runs the register-prefetch kernel of each order
+    # at a fixed tile; plans of that tile must be buildable in every precision the
+    # schedule takes (host-only queries: no device is touched)
+    from paper_1809_05471_gb300 import build
+    from paper_1809_05471_gb300 import igasf as G
+    build.build()
+    for prec in (G.FP32, G.BF16):
+        for p in range(2, 7):
+            tile = list(G.batch_persistent_tile(p, prec))
+            cands = [(list(t), v) for t, v in G.list_kernels(3, p, prec)]
+            assert (tile, G.KERNEL_REGISTERS) in cands, (prec, p, tile, cands)
