@@ -2,8 +2,8 @@
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
 // BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
-//   FP32: register prefetch, tile 4, 4, 4, registers capped for 4 resident blocks (mass 6, FP32), tables reloaded for the transposed sweep; BF16: register prefetch, tile 4, 4, 8 (mass 6, FP32)
-//   FP32: register prefetch, tile 4, 4, 8, registers capped for 4 resident blocks (mass 6, FP32), tables reloaded for the transposed sweep; BF16: register prefetch, tile 4, 4, 4 (mass 6, FP32)
+//   FP32: register prefetch, tile 4, 4, 4, registers capped for 4 resident blocks (mass 6, FP32), tables reloaded for the transposed sweep; BF16: register prefetch, tile 4, 4, 8
+//   FP32: register prefetch, tile 4, 4, 8, registers capped for 4 resident blocks (mass 6, FP32), tables reloaded for the transposed sweep; BF16: register prefetch, tile 4, 4, 4
 //   TMA ring, tile 8, 4, 2
 //   TMA ring, tile 4, 4, 4
 //   register prefetch, tile 4, 4, 1

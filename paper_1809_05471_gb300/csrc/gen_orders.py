@@ -95,16 +95,16 @@ def generate(outdir=HERE):
              "// FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep",
              "// of tile shapes and factor-stream variants on the order-sweep workload);",
              "// BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:"]
-        def describe(c):
+        def describe(c, bf=False):
             v, t = c[0], c[1]
-            mbm = mass_minb.get((P, t), 0) if v == R else 0
+            mbm = mass_minb.get((P, t), 0) if v == R and not bf else 0
             return "%s, tile %s%s%s%s%s" % (name[v], t, (", registers capped for %d resident blocks" % c[2]) if len(c) > 2 and c[2] else "",
                                            (" (mass %d, FP32)" % mbm) if mbm else "",
                                            ", tables reloaded for the transposed sweep" if len(c) > 3 and c[3] else "",
                                            " (BF16 too)" if len(c) > 4 and c[4] else "")
         for c in main[P]:
             if c[0] == "pair":
-                L.append("//   FP32: %s; BF16: %s" % (describe(c[1]), describe(c[2])))
+                L.append("//   FP32: %s; BF16: %s" % (describe(c[1]), describe(c[2], bf=True)))
             else:
                 L.append("//   %s" % describe(c))
         L.append("// Register-prefetch kernels request their tile's factors into L2 at entry: "
