@@ -2,8 +2,8 @@
 // FP32 (packed FP32x2) candidates, the first the default (fastest in a sweep
 // of tile shapes and factor-stream variants on the order-sweep workload);
 // BF16 (bfloat16-stored factors) uses the same candidates unless a line names both:
-//   register prefetch, tile 2, 2, 6, registers capped for 2 resident blocks, tables reloaded for the transposed sweep (BF16 too)
-//   register prefetch, tile 2, 2, 8, registers capped for 2 resident blocks, tables reloaded for the transposed sweep
+//   FP32: register prefetch, tile 2, 2, 8, registers capped for 2 resident blocks, tables reloaded for the transposed sweep; BF16: register prefetch, tile 2, 2, 6, registers capped for 2 resident blocks, tables reloaded for the transposed sweep (BF16 too)
+//   FP32: register prefetch, tile 2, 2, 6, registers capped for 2 resident blocks, tables reloaded for the transposed sweep (BF16 too); BF16: register prefetch, tile 2, 2, 8
 //   register prefetch, tile 2, 2, 2, registers capped for 2 resident blocks, tables reloaded for the transposed sweep
 //   TMA ring, tile 2, 2, 2
 // Register-prefetch kernels request their tile's factors into L2 at entry: FP32 yes, BF16 yes.
@@ -32,13 +32,12 @@ int apply3d_p9(int prec, ApplyKernel *out, int max_out) {
   }
   const bool bf = prec == IGASF_BF16;
 #ifndef IGASF_TILE_SEARCH
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 6, true, 2, 2, 3>() : make_apply3d_f32r<9, 2, 2, 6, false, 2, 2, 3>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 8, true, 2, 0, 2>() : make_apply3d_f32r<9, 2, 2, 8, false, 2, 2, 3>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 6, true, 2, 2, 3>() : make_apply3d_f32r<9, 2, 2, 8, false, 2, 2, 3>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 8, true, 2, 0, 2>() : make_apply3d_f32r<9, 2, 2, 6, false, 2, 2, 3>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 2, true, 2, 0, 2>() : make_apply3d_f32r<9, 2, 2, 2, false, 2, 2, 3>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32<9, 2, 2, 2, true>() : make_apply3d_f32<9, 2, 2, 2>();
 #else
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 6, true, 2, 2, 3>() : make_apply3d_f32r<9, 2, 2, 6, false, 2, 2, 3>();
-  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 8, true>() : make_apply3d_f32r<9, 2, 2, 8>();
+  if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 6, true, 2, 2, 3>() : make_apply3d_f32r<9, 2, 2, 8, false, 2, 2, 3>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 4, true>() : make_apply3d_f32r<9, 2, 2, 4>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 2, 2, true>() : make_apply3d_f32r<9, 2, 2, 2>();
   if (n < max_out) out[n++] = bf ? make_apply3d_f32r<9, 2, 1, 2, true>() : make_apply3d_f32r<9, 2, 1, 2>();

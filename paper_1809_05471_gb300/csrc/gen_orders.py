@@ -31,10 +31,11 @@ main = {
      (T, "8, 4, 2"), (T, "4, 4, 4"), (R, "4, 4, 1")],
  5: [("pair", (T, "4, 4, 4"), (R, "4, 2, 8")), (R, "4, 4, 4"), (R, "4, 2, 4"), ("pair", (R, "4, 2, 8"), (T, "4, 4, 4"))],
  6: [(R, "2, 2, 8", 4, 1, 1), (R, "2, 2, 2", 4), (R, "4, 4, 2"), (T, "4, 2, 2")],
- 7: [("pair", (R, "2, 2, 6", 3, 1), (R, "2, 2, 8")), ("pair", (R, "2, 2, 8", 3, 1), (R, "2, 2, 6")),
+ 7: [("pair", (R, "2, 2, 8", 3, 1), (R, "2, 2, 8")), ("pair", (R, "2, 2, 6", 3, 1), (R, "2, 2, 6")),
      (T, "2, 2, 4", 0, 1), (R, "4, 2, 2")],
  8: [(R, "2, 2, 8"), (R, "2, 2, 6"), (R, "2, 2, 2"), (T, "4, 2, 1")],
- 9: [(R, "2, 2, 6", 2, 1, 1), (R, "2, 2, 8", 2, 1), (R, "2, 2, 2", 2, 1), (T, "2, 2, 2")],
+ 9: [("pair", (R, "2, 2, 8", 2, 1), (R, "2, 2, 6", 2, 1, 1)), ("pair", (R, "2, 2, 6", 2, 1, 1), (R, "2, 2, 8")),
+     (R, "2, 2, 2", 2, 1), (T, "2, 2, 2")],
 }
 search = {
  2: ["8, 8, 2", "8, 8, 4", "16, 8, 4", "8, 4, 8", "8, 8, 8", "16, 8, 2"],
@@ -85,7 +86,10 @@ mass_minb = {(4, "4, 4, 4"): 6, (4, "4, 4, 8"): 6}
 # p = 4 spills at 4 blocks: 0.493 -> 0.575). Caps re-measured too: p = 7 FP32
 # 3 blocks instead of 2 (168 registers, 4 bytes spilled; 2M dofs 3.61 -> 3.36 ms);
 # BF16 p = 6 at 5 blocks and p = 7 at 3 blocks (with reload) were slower (1.78 ->
-# 1.94, 2.72 -> 2.91 ms), p = 8 spills at any cap, p = 9 at 3 blocks spills 5 KB
+# 1.94, 2.72 -> 2.91 ms), p = 8 spills at any cap, p = 9 at 3 blocks spills 5 KB.
+# FP32 p = 7 and 9 then default to 2x2x8 (p = 7: stiffness 3.45 ms either way, mass
+# 1.27 -> 1.17 ms; p = 9: stiffness 7.95 -> 7.83 ms, mass 3.03 -> 2.95 ms); BF16
+# keeps 2x2x6 at p = 9 (2x2x8: 10.8 ms)
 mk = {R: "make_apply3d_f32r", T: "make_apply3d_f32"}
 name = {R: "register prefetch", T: "TMA ring"}
 def generate(outdir=HERE):
