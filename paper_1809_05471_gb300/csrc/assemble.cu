@@ -357,17 +357,17 @@ int64_t pattern_1d(const igasf_plan *h, int a, std::vector<int> &lo, std::vector
 }  // namespace
 }  // namespace igasf
 
-extern "C" int64_t igasf_assembled_nnz(igasf_handle h) {
+extern "C" int64_t igasf_assembled_nnz(igasf_handle h) try {
   using namespace igasf;
   if (!h) return set_error(IGASF_ERR_INVALID_ARG, "handle is NULL");
   int64_t nnz = 1;
   std::vector<int> lo, cnt;
   for (int a = 0; a < h->d; ++a) nnz *= pattern_1d(h, a, lo, cnt);
   return nnz;
-}
+} IGASF_CATCH_HOST
 
 extern "C" int igasf_assemble_csr(igasf_handle h, int op, int64_t *rowptr, int64_t *colind,
-                                  double *values, size_t workspace_limit_bytes, void *stream) {
+                                  double *values, size_t workspace_limit_bytes, void *stream) try {
   using namespace igasf;
   if (!h || !rowptr || !colind || !values)
     return set_error(IGASF_ERR_INVALID_ARG, "handle, rowptr, colind and values must be non-NULL");
@@ -500,4 +500,4 @@ extern "C" int igasf_assemble_csr(igasf_handle h, int op, int64_t *rowptr, int64
   if (e != cudaSuccess)
     return set_error(IGASF_ERR_CUDA, (std::string("assembly: ") + cudaGetErrorString(e)).c_str());
   return IGASF_OK;
-}
+} IGASF_CATCH_HOST

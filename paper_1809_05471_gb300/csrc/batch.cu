@@ -180,8 +180,10 @@ int igasf_batch_create(int nplans, const igasf_handle *plans, int op, int prec, 
   return igasf_batch_create_ex(nplans, plans, op, prec, IGASF_BATCH_GRAPH, out);
 }
 
-int igasf_batch_create_ex(int nplans, const igasf_handle *plans, int op, int prec, int schedule,
-                          igasf_batch *out) {
+// The body of igasf_batch_create_ex; *created receives the batch as soon as it
+// exists (its error paths free it themselves).
+static int batch_create_impl(int nplans, const igasf_handle *plans, int op, int prec, int schedule,
+                             igasf_batch *out, igasf_batch *created) {
   using namespace igasf;
   if (!out || !plans || nplans < 1) return set_error(IGASF_ERR_INVALID_ARG, "need nplans >= 1, plans and out");
   if (op != IGASF_MASS && op != IGASF_STIFFNESS) return set_error(IGASF_ERR_INVALID_ARG, "bad op");
@@ -207,6 +209,7 @@ int igasf_batch_create_ex(int nplans, const igasf_handle *plans, int op, int pre
   }
   igasf_batch b = new (std::nothrow) igasf_batch_s();
   if (!b) return set_error(IGASF_ERR_OOM, "host allocation");
+  *created = b;
   b->persistent = pers;
   b->n = nplans;
   b->op = op;
@@ -327,15 +330,31 @@ int igasf_batch_create_ex(int nplans, const igasf_handle *plans, int op, int pre
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
   if (e != cudaSuccess) {
+    // the message first (it can throw), then the batch
+    const int rc = set_error(e == cudaErrorMemoryAllocation ? IGASF_ERR_OOM : IGASF_ERR_CUDA,
+                             (std::string("batch set-up: ") + cudaGetErrorString(e)).c_str());
     free_batch(b);
-    return set_error(e == cudaErrorMemoryAllocation ? IGASF_ERR_OOM : IGASF_ERR_CUDA,
-                     (std::string("batch set-up: ") + cudaGetErrorString(e)).c_str());
+    return rc;
   }
   *out = b;
   return IGASF_OK;
 }
 
-int igasf_batch_apply(igasf_batch b, const void *u, void *v, void *stream) {
+int igasf_batch_create_ex(int nplans, const igasf_handle *plans, int op, int prec, int schedule,
+                          igasf_batch *out) {
+  igasf_batch created = nullptr;
+  try {
+    return batch_create_impl(nplans, plans, op, prec, schedule, out, &created);
+  } catch (const std::bad_alloc &) {
+    if (created) free_batch(created);
+    return igasf::set_error(IGASF_ERR_OOM, "host allocation failed while creating the batch");
+  } catch (...) {
+    if (created) free_batch(created);
+    return igasf::set_error(IGASF_ERR_INVALID_ARG, "unexpected host exception while creating the batch");
+  }
+}
+
+int igasf_batch_apply(igasf_batch b, const void *u, void *v, void *stream) try {
   using namespace igasf;
   if (!b || !u || !v) return set_error(IGASF_ERR_INVALID_ARG, "batch, u and v must be non-NULL");
   const size_t es = b->prec == IGASF_FP64 ? 8 : 4;
@@ -351,7 +370,7 @@ int igasf_batch_apply(igasf_batch b, const void *u, void *v, void *stream) {
   if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return set_error(IGASF_ERR_CUDA, (std::string("batch apply: ") + cudaGetErrorString(e)).c_str());
   return IGASF_OK;
-}
+} IGASF_CATCH_HOST
 
 int igasf_batch_info(igasf_batch b, int64_t *total_dofs, int64_t *total_quad_points,
                      int64_t *factor_bytes, int *launch_groups) {
@@ -383,7 +402,7 @@ int igasf_batch_destroy(igasf_batch b) {
 extern "C" int igasf_autotune(int d, const int *orders, const int *knot_lengths,
                               const double *const *knots, const double *ctrl, const igasf_coef *coef,
                               int op, int prec, int repeats, int *tile, int *kernel_variant,
-                              double *best_ms) {
+                              double *best_ms) try {
   using namespace igasf;
   if (!tile || !kernel_variant || !orders || repeats < 1)
     return set_error(IGASF_ERR_INVALID_ARG, "need orders, tile, kernel_variant and repeats >= 1");
@@ -443,4 +462,4 @@ extern "C" int igasf_autotune(int d, const int *orders, const int *knot_lengths,
   *kernel_variant = cand[best_i].variant;
   if (best_ms) *best_ms = best;
   return IGASF_OK;
-}
+} IGASF_CATCH_HOST

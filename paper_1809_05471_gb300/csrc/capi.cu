@@ -258,9 +258,13 @@ int igasf_list_kernels(int d, int p, int prec, int geometry, int *tiles, int *va
   return n;
 }
 
-int igasf_setup(int d, const int *orders, const int *knot_lengths, const double *const *knots,
-                const double *ctrl, const igasf_coef *coef, const igasf_options *opt,
-                igasf_handle *out) {
+// The body of igasf_setup. *created receives the plan as soon as it exists; the
+// error paths free it themselves (after recording their message, the last step
+// that can throw), and igasf_setup frees it if a host exception interrupts the
+// setup.
+static int setup_impl(int d, const int *orders, const int *knot_lengths, const double *const *knots,
+                      const double *ctrl, const igasf_coef *coef, const igasf_options *opt,
+                      igasf_handle *out, igasf_plan **created) {
   g_last_error.clear();
   if (!out) return fail(IGASF_ERR_INVALID_ARG, "out is NULL");
   if (d != 2 && d != 3) return fail(IGASF_ERR_UNSUPPORTED, "d = %d; supported: 2, 3", d);
@@ -338,6 +342,7 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
   // host-side validation done: now the device
   igasf_plan *h = new (std::nothrow) igasf_plan();
   if (!h) return fail(IGASF_ERR_OOM, "host allocation");
+  *created = h;
   h->d = d;
   h->p = p;
   h->default_prec = o.default_prec;
@@ -526,14 +531,30 @@ int igasf_setup(int d, const int *orders, const int *knot_lengths, const double 
     return rc;
   }
   if (bad) {
+    const int rc = fail(IGASF_ERR_GEOMETRY, "det J <= 0 at some quadrature point: G is not orientation preserving");
     free_plan(h);
-    return fail(IGASF_ERR_GEOMETRY, "det J <= 0 at some quadrature point: G is not orientation preserving");
+    return rc;
   }
   // locate the static scratch of igasf_apply_noalloc on this device now, so
   // that its first call allocates nothing (noalloc.cu)
   noalloc_prepare(h->device);
   *out = h;
   return IGASF_OK;
+}
+
+int igasf_setup(int d, const int *orders, const int *knot_lengths, const double *const *knots,
+                const double *ctrl, const igasf_coef *coef, const igasf_options *opt,
+                igasf_handle *out) {
+  igasf_plan *created = nullptr;
+  try {
+    return setup_impl(d, orders, knot_lengths, knots, ctrl, coef, opt, out, &created);
+  } catch (const std::bad_alloc &) {
+    if (created) free_plan(created);
+    return fail(IGASF_ERR_OOM, "host allocation failed during setup");
+  } catch (...) {
+    if (created) free_plan(created);
+    return fail(IGASF_ERR_INVALID_ARG, "unexpected host exception during setup");
+  }
 }
 
 int igasf_apply_prec(igasf_handle h, int op, int prec, const void *u, void *v, void *stream) {
@@ -735,7 +756,7 @@ int igasf_describe(igasf_handle h, int prec, igasf_plan_desc *out) {
 }
 
 int igasf_get_tables(igasf_handle h, int dir, double *nodes, double *weights, double *B,
-                     double *dB) {
+                     double *dB) try {
   if (!h) return fail(IGASF_ERR_INVALID_ARG, "handle is NULL");
   if (dir < 0 || dir >= h->d) return fail(IGASF_ERR_INVALID_ARG, "dir = %d", dir);
   // output: the non-empty spans' points, i.e. full point elem[i] p + g for API point i p + g
@@ -760,9 +781,9 @@ int igasf_get_tables(igasf_handle h, int dir, double *nodes, double *weights, do
   }
   if (e != cudaSuccess) return cuda_fail(e, "copy tables");
   return IGASF_OK;
-}
+} IGASF_CATCH_HOST
 
-int igasf_quad_points(igasf_handle h, double *xyz_host) {
+int igasf_quad_points(igasf_handle h, double *xyz_host) try {
   if (!h || !xyz_host) return fail(IGASF_ERR_INVALID_ARG, "handle or xyz_host is NULL");
   GeometryParams g;
   memset(&g, 0, sizeof(g));
@@ -780,6 +801,8 @@ int igasf_quad_points(igasf_handle h, double *xyz_host) {
   g.coef_const = 1.0;
   g.nout = 0;
   const size_t bytes = sizeof(double) * (size_t)h->Qtot * h->d;
+  // host buffer first: nothing on the device is left behind if it cannot be had
+  std::vector<double> full(h->empty_spans ? (size_t)h->Qtot * h->d : 0);
   double *tmp = nullptr;
   unsigned int *bad = nullptr;
   cudaError_t e = cudaMalloc((void **)&tmp, bytes);
@@ -792,7 +815,6 @@ int igasf_quad_points(igasf_handle h, double *xyz_host) {
   }
   if (e == cudaSuccess) {
     if (h->empty_spans) {
-      std::vector<double> full((size_t)h->Qtot * h->d);
       e = cudaMemcpy(full.data(), tmp, bytes, cudaMemcpyDeviceToHost);
       if (e == cudaSuccess) compact_qp(h, full.data(), xyz_host, h->d);
     } else {
@@ -803,9 +825,9 @@ int igasf_quad_points(igasf_handle h, double *xyz_host) {
   cudaFree(bad);
   if (e != cudaSuccess) return cuda_fail(e, "quadrature points");
   return IGASF_OK;
-}
+} IGASF_CATCH_HOST
 
-int igasf_get_factors(igasf_handle h, int op, int prec, double *out) {
+int igasf_get_factors(igasf_handle h, int op, int prec, double *out) try {
   if (!h || !out) return fail(IGASF_ERR_INVALID_ARG, "handle or out is NULL");
   if (op != IGASF_MASS && op != IGASF_STIFFNESS) return fail(IGASF_ERR_INVALID_ARG, "op = %d", op);
   if (prec < 0 || prec >= kNumPrec || !h->var[prec].present)
@@ -814,13 +836,13 @@ int igasf_get_factors(igasf_handle h, int op, int prec, double *out) {
     return fail(IGASF_ERR_UNSUPPORTED, "precision %d evaluates its factors on the fly: none are stored", prec);
   const int nf = num_fields(h->d, op);
   const size_t bytes = sizeof(double) * (size_t)h->Qtot * nf;
+  std::vector<double> full(h->empty_spans ? (size_t)h->Qtot * nf : 0);   // host buffer first
   double *tmp = nullptr;
   cudaError_t e = cudaMalloc((void **)&tmp, bytes);
   if (e != cudaSuccess) return cuda_fail(e, "export buffer");
   e = launch_export_factors(h->var[prec].L, op, h->Qtot, h->Q, tmp, nullptr);
   if (e == cudaSuccess) {
     if (h->empty_spans) {
-      std::vector<double> full((size_t)h->Qtot * nf);
       e = cudaMemcpy(full.data(), tmp, bytes, cudaMemcpyDeviceToHost);
       if (e == cudaSuccess) compact_qp(h, full.data(), out, nf);
     } else {
@@ -830,6 +852,6 @@ int igasf_get_factors(igasf_handle h, int op, int prec, double *out) {
   cudaFree(tmp);
   if (e != cudaSuccess) return cuda_fail(e, "export factors");
   return IGASF_OK;
-}
+} IGASF_CATCH_HOST
 
 }  // extern "C"

@@ -5,11 +5,26 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <new>
 #include <vector>
 
 #include "igasf.h"
 
 namespace igasf {
+
+// Records the message of the last error (thread-local) and returns code.
+int set_error(int code, const char *msg);
+
+// C-ABI entry points that use standard containers end in this handler of a
+// function-try-block, so that a failed host allocation returns IGASF_ERR_OOM
+// instead of letting an exception cross the C boundary.
+#define IGASF_CATCH_HOST                                                          \
+  catch (const std::bad_alloc &) {                                                \
+    return igasf::set_error(IGASF_ERR_OOM, "host allocation failed");             \
+  }                                                                               \
+  catch (...) {                                                                   \
+    return igasf::set_error(IGASF_ERR_INVALID_ARG, "unexpected host exception");  \
+  }
 
 constexpr int kMaxDim = 3;
 constexpr int kNumPrec = 5;        // FP64, FP32, BF16, TF32, BF16_MMA

@@ -306,7 +306,7 @@ bool residual(Ctx &c, const double *b, const double *x, double *rn) {
 
 extern "C" int igasf_cg_solve(igasf_handle h, int inner_prec, const double *b, double *x,
                               double rtol, double inner_rtol, int max_iterations,
-                              igasf_cg_report *report, void *stream) {
+                              igasf_cg_report *report, void *stream) try {
   using namespace igasf;
   if (!h || !b || !x) return set_error(IGASF_ERR_INVALID_ARG, "handle, b and x must be non-NULL");
   if (h->d != 3) return set_error(IGASF_ERR_UNSUPPORTED, "the solver handles d = 3 plans");
@@ -427,4 +427,4 @@ extern "C" int igasf_cg_solve(igasf_handle h, int inner_prec, const double *b, d
   w.release();
   if (report) *report = rep;
   return IGASF_OK;
-}
+} IGASF_CATCH_HOST
