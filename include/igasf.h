@@ -58,6 +58,8 @@ typedef enum {
   IGASF_ERR_OOM = -6,         /* device or host allocation failed */
   IGASF_ERR_TIMEOUT = -7      /* a bounded device wait gave up */
 } igasf_status;
+/* Every call reports failures through these codes (and igasf_last_error_message);
+ * no C++ exception leaves the library. */
 
 typedef enum { IGASF_MASS = 0, IGASF_STIFFNESS = 1 } igasf_op;
 
@@ -246,7 +248,7 @@ int igasf_describe(igasf_handle h, int prec, igasf_plan_desc *out);
  * value of the j-th function active on the element of quadrature point q
  * (function index = k - p + 1 + j for the element's span [t_k, t_k+1), 0-based
  * knots; element index + j for simple knots) and dB its derivative. Host
- * outputs; any may be NULL. Synchronous.
+ * outputs; any may be NULL. Synchronous. Errors: INVALID_ARG, CUDA, OOM.
  */
 int igasf_get_tables(igasf_handle h, int dir, double *nodes, double *weights, double *B,
                      double *dB);
@@ -256,6 +258,8 @@ int igasf_get_tables(igasf_handle h, int dir, double *nodes, double *weights, do
  * lexicographic quadrature order: mass out[q]; stiffness out[q*nf + f] with
  * nf = d(d+1)/2 upper-triangle entries in row order (11,12,13,22,23,33 or
  * 11,12,22). Host output of num_quad_points*nf doubles. Synchronous.
+ * Errors: INVALID_ARG, UNSUPPORTED (precision not stored, or factors evaluated
+ * on the fly), CUDA, OOM.
  */
 int igasf_get_factors(igasf_handle h, int op, int prec, double *out);
 
