@@ -43,3 +43,18 @@ def test_full_size_csr_repeats_the_sample_rows():
     y = O.spmv(*big, u)
     ys = O.spmv(rp, ci, va, u)
     assert np.array_equal(y, np.tile(ys, 3)[:95])
+
+
+def test_algorithmic_bytes_are_the_stated_per_unit_figures():
+    # the roofline's bytes per launch: every stored factor once, u once, v once;
+    # per quadrature point and per dof as stated for each precision and operator
+    import bench
+    per_qp = {("stiffness", "fp32"): 24, ("stiffness", "fp64"): 48, ("stiffness", "bf16"): 12,
+              ("mass", "fp32"): 4, ("mass", "fp64"): 8, ("mass", "bf16"): 2}
+    per_dof = {"fp32": 8, "fp64": 16, "bf16": 8}
+    for (op, prec), b in per_qp.items():
+        assert bench.algorithmic_bytes(op, prec, 1, 0) == b, (op, prec)
+        assert bench.algorithmic_bytes(op, prec, 0, 1) == per_dof[prec], (op, prec)
+    assert bench.algorithmic_bytes("stiffness", "fp32", 1, 0, d=2) == 12   # 3 fields in 2D
+    # the 64^3, p = 4 headline: 256^3 Gauss points and 67^3 dofs
+    assert bench.algorithmic_bytes("stiffness", "fp32", 256 ** 3, 67 ** 3) == 405059288
